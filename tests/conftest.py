@@ -1,0 +1,19 @@
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def pytest_configure(config):
+    config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a)")
+    config.addinivalue_line("markers", "slow: long-running statistical check")
+
+
+def pytest_collection_modifyitems(config, items):
+    # test files named test_zz_* run last (pytest sorts by file name already;
+    # this keeps it explicit when files are passed in another order)
+    items.sort(key=lambda it: (os.path.basename(str(it.fspath)).startswith("test_zz_"),))
