@@ -1,0 +1,421 @@
+"""Throughput of the PTHR hot path on GB300.
+
+Workload (one "step" = one EMCS of the whole batch): PTHR at L=16 with 512
+disorder samples x 32 temperatures 0.2..1.6 x 4 replica groups, plus 4
+reservoir clones per group at T_max; per EMCS 10 Metropolis sweeps of every
+PT clone and 240 of every reservoir clone, the all-cluster Houdayer update at
+every T < 1, one PT round and one ER exchange, then the measurement.  The
+reservoir is pre-thermalised with 960 sweeps before the warm-up.
+
+Metric: spin updates per ns (PT and reservoir updates summed) for the whole
+job, with EMCS/s ("PTHR sweeps/s"), Houdayer pair moves/s and the plain
+one-sample-per-launch form reported beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun (N > 1) every rank runs its own 512 samples (weak scaling,
+no collective on the data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "spin updates/ns and PTHR sweeps/s at L=16 (FP32 batched vs plain)"
+UNIT = "spin-updates/ns"
+WL = W.WORKLOADS["c4"]
+# Algorithmic ALU work of one Metropolis spin update: a
+# quarter of a Philox4x32-10 call (10 rounds x (4 multiply halves + 2
+# three-input XORs) / 4 = 15), the 24-bit uniform (2), the local field
+# (6 FMA), -beta dE (2 FMUL), the exponential (1), the two comparisons (2)
+# and the conditional flip (1).
+OPS_PER_UPDATE = 29
+# shared-memory bytes of one update in the packed colour-row layout: the
+# 4-site word of the site and its 6 neighbours are read and the site word is
+# written once per 4 updates (8 x 4 B / 4).
+SMEM_BYTES_PER_UPDATE = 8
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (FileNotFoundError, OSError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def batch_config(n_samples=None):
+    from paper_2605_25872_gb300 import BatchConfig
+    return BatchConfig(L=WL.L, n_samples=n_samples or WL.n_samples, n_temps=WL.n_temps,
+                       t_min=WL.t_min, t_max=WL.t_max, n_replicas=WL.n_replicas, n_res=WL.n_res,
+                       sweeps_per_emcs=WL.sweeps_per_emcs,
+                       res_sweeps_per_emcs=WL.res_sweeps_per_emcs, er_on=WL.er_on, cluster="acu")
+
+
+def updates_per_emcs(n_samples):
+    V = WL.V
+    pt = n_samples * WL.n_replicas * WL.n_temps * WL.sweeps_per_emcs * V
+    res = n_samples * WL.n_replicas * WL.n_res * WL.res_sweeps_per_emcs * V
+    return pt, res
+
+
+def n_acu_temps():
+    T = [WL.t_min + k * (WL.t_max - WL.t_min) / (WL.n_temps - 1) for k in range(WL.n_temps)]
+    return sum(1 for t in T if t < 1.0)
+
+
+# ----------------------------------------------------------------------------- CPU legs
+
+def oracle_sample_run(n_threads, n_emcs=1, seed_offset=0):
+    """The FP64 oracle, as it stands, on `n_threads` samples of the workload,
+    one EMCS each, in parallel host threads.  Returns (updates, seconds)."""
+    import oracle as O
+    J = W.gaussian_couplings(WL.L, n_threads, W.batch_seed(WL.index) + 17 + seed_offset)
+    smps = [O.OracleSample(WL.L, WL.n_temps, WL.t_min, WL.t_max, W.batch_seed(WL.index) + s,
+                           J=J[s].astype(np.float64), n_groups=WL.n_replicas, n_res=WL.n_res,
+                           sweeps_per_emcs=WL.sweeps_per_emcs,
+                           res_sweeps_per_emcs=WL.res_sweeps_per_emcs)
+            for s in range(n_threads)]
+    t0 = time.perf_counter()
+    used = O.run_samples_threaded(smps, n_emcs, n_threads)
+    dt = time.perf_counter() - t0
+    pt, res = updates_per_emcs(used)
+    return (pt + res) * n_emcs, dt, used
+
+
+def cpu_baseline():
+    cores = os.cpu_count() or 1
+    upd, dt, used = oracle_sample_run(cores)
+    return {"value": upd / (dt * 1e9), "unit": UNIT, "cores": used, "kind": "oracle",
+            "sample": f"{used} samples x 1 EMCS of the L=16 workload (one sample per host thread), "
+                      f"{upd:.3g} spin updates in {dt:.1f} s"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    cores = os.cpu_count() or 1
+    for _ in range(args.warmup if args.warmup < 1 else 1):
+        oracle_sample_run(min(cores, 2))
+    times, upd_total = [], 0
+    for k in range(args.steps):
+        upd, dt, used = oracle_sample_run(cores, seed_offset=k)
+        times.append(dt)
+        upd_total += upd
+    value = upd_total / (sum(times) * 1e9)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_dict(),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"each step: {cores} samples x 1 EMCS of the workload, one per host thread"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def config_dict():
+    return {"workload": f"{WL.name} (L={WL.L}, {WL.n_samples} samples x {WL.n_temps} T "
+                        f"[{WL.t_min},{WL.t_max}] x {WL.n_replicas} replicas + {WL.n_res} reservoir "
+                        f"clones/group; EMCS = {WL.sweeps_per_emcs} sweeps + ACU(T<1) + PT + ER "
+                        f"({WL.res_sweeps_per_emcs} reservoir sweeps))",
+            "L": WL.L, "n_samples": WL.n_samples, "n_temps": WL.n_temps, "n_replicas": WL.n_replicas,
+            "n_res": WL.n_res, "sweeps_per_emcs": WL.sweeps_per_emcs,
+            "res_sweeps_per_emcs": WL.res_sweeps_per_emcs, "update_rule": "metropolis",
+            "couplings": "N(0,1) on the 2^-18 grid (seeded)",
+            "l2": "inputs larger than L2: 330 MB of resident state per GPU"}
+
+
+# ----------------------------------------------------------------------------- GPU arm
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2605_25872_gb300 import Batch
+    from paper_2605_25872_gb300.build import build
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if rank == 0 or world == 1:
+        build()
+    if world > 1:
+        dist.barrier()
+        build()
+
+    cfg = batch_config()
+    S = cfg.n_samples
+    seeds = W.sample_seeds(W.batch_seed(WL.index) + rank * S, S)
+    J = W.gaussian_couplings(WL.L, S, W.batch_seed(WL.index) + rank)
+    stream = torch.cuda.Stream(dev)
+    b = Batch(cfg, couplings=J, seeds=seeds, device=dev, stream=stream)
+    b.prethermalize(WL.res_pretherm_sweeps)
+    pt_upd, res_upd = updates_per_emcs(S)
+    upd = pt_upd + res_upd
+
+    # ---- warm-up
+    for _ in range(args.warmup):
+        b.emcs(1)
+    stream.synchronize()
+
+    # ---- timed region: the EMCS as its four C-ABI calls, CUDA events between
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
+    sampler = ClockSampler(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    sampler.start()
+    time.sleep(0.3)
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        t_start.record(stream)
+        for k in range(args.steps):
+            e = ev[k]
+            e[0].record(stream)
+            b.sweep(WL.sweeps_per_emcs, WL.res_sweeps_per_emcs)
+            e[1].record(stream)
+            b.houdayer()
+            e[2].record(stream)
+            b.swap(True, True)
+            e[3].record(stream)
+            b.measure()
+            e[4].record(stream)
+        t_end.record(stream)
+    stream.synchronize()
+    torch.cuda.synchronize(dev)
+    clocks = sampler.stop()
+    ms_total = t_start.elapsed_time(t_end)
+    if world > 1:
+        t = torch.tensor([ms_total], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+        dist.barrier()
+    phase = np.array([[e[i].elapsed_time(e[i + 1]) for i in range(4)] for e in ev])
+    ms_sweep = float(phase[:, 0].mean())
+    ms_step = ms_total / args.steps
+    value = world * upd * args.steps / (ms_total * 1e6)
+    assert b.poll(60000) == 0
+
+    # ---- graph replay of whole EMCS (same kernels, one launch per EMCS)
+    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    b.emcs(1, graph=True)
+    stream.synchronize()
+    n_graph = max(2, min(args.steps, 10))
+    with torch.cuda.stream(stream):
+        g0.record(stream)
+        b.emcs(n_graph, graph=True)
+        g1.record(stream)
+    stream.synchronize()
+    ms_graph = g0.elapsed_time(g1) / n_graph
+
+    result = None
+    if rank == 0:
+        pk, pk_kind = peaks()
+        sm_max = float(pk.get("sm_max_mhz", 2070.0))
+        n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+        alu_peak = n_sm * 128 * sm_max * 1e6 / 1e12                # T lane-ops/s
+        achieved_ops = OPS_PER_UPDATE * upd / (ms_sweep * 1e-3) / 1e12
+        smem_peak = n_sm * 128 * sm_max * 1e6 / 1e12                # TB/s (128 B/clk/SM)
+        achieved_smem = SMEM_BYTES_PER_UPDATE * upd / (ms_sweep * 1e-3) / 1e12
+        traffic = None
+        tr_path = os.path.join(ROOT, "profiles", "sweep_kernel_L16_traffic.json")
+        if os.path.exists(tr_path):
+            with open(tr_path) as f:
+                tr = json.load(f)
+            if tr.get("kernel_version") == kernel_version():
+                traffic = tr.get("dram_bytes_per_launch")
+        pairs = S * (WL.n_replicas // 2) * n_acu_temps()
+        plain = plain_form(dev, upd / S, seeds, J)
+        e2e = end_to_end(dev, cfg, J, seeds, args.steps)
+        result = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": config_dict(),
+            "emcs_per_s": world * 1e3 / ms_step,
+            "emcs_per_s_graph": world * 1e3 / ms_graph,
+            "updates_per_ns_graph": world * upd / (ms_graph * 1e6),
+            "pt_updates_per_emcs": pt_upd, "res_updates_per_emcs": res_upd,
+            "houdayer_pair_moves_per_s": world * pairs * 1e3 / ms_step,
+            "phase_ms": {"sweep": ms_sweep, "houdayer": float(phase[:, 1].mean()),
+                         "swap": float(phase[:, 2].mean()), "measure": float(phase[:, 3].mean())},
+            "plain": plain,
+            "roofline": {"kernel": "sweep_kernel<16, Metropolis>", "bound": "alu",
+                         "achieved": achieved_ops, "peak": alu_peak, "unit": "Tops/s",
+                         "frac": achieved_ops / alu_peak, "traffic": traffic,
+                         "ops_per_update": OPS_PER_UPDATE,
+                         "peak_basis": f"{n_sm} SMs x 128 FP32/INT32 lanes x {sm_max:.0f} MHz "
+                                       f"(sm_max_mhz, {pk_kind})",
+                         "smem": {"achieved_TBps": achieved_smem, "peak_TBps": smem_peak,
+                                  "frac": achieved_smem / smem_peak,
+                                  "bytes_per_update": SMEM_BYTES_PER_UPDATE}},
+            "gpu_launches": 4 * args.steps,
+            "cpu_baseline": cpu_baseline(),
+            "e2e": e2e,
+            "clocks": clocks,
+        }
+        print(json.dumps(result))
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def kernel_version():
+    """Hash of the sweep kernel source: a stored DRAM-traffic figure is only
+    valid for the kernel it was measured on."""
+    import hashlib
+    h = hashlib.sha1()
+    for f in ("sweep.cu", "pthr_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_2605_25872_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:12]
+
+
+def plain_form(dev, upd_per_sample, seeds, J, n=32):
+    """The same kernels with one sample per launch sequence and no graph,
+    looped over samples (a bounded sample of n of the 512, scaled)."""
+    import torch
+    from paper_2605_25872_gb300 import Batch
+    cfg = batch_config(1)
+    stream = torch.cuda.Stream(dev)
+    bs = [Batch(cfg, couplings=J[s:s + 1], seeds=seeds[s:s + 1], device=dev, stream=stream)
+          for s in range(n)]
+    for x in bs:
+        x.prethermalize(WL.res_pretherm_sweeps)
+        x.emcs(1)
+    stream.synchronize()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        t0.record(stream)
+        for x in bs:
+            x.emcs(1, graph=False)
+        t1.record(stream)
+    stream.synchronize()
+    ms = t0.elapsed_time(t1)
+    ms_512 = ms * WL.n_samples / n
+    for x in bs:
+        x.close()
+    return {"updates_per_ns": upd_per_sample * n / (ms * 1e6),
+            "emcs_per_s_512_samples": 1e3 / ms_512,
+            "sample": f"{n} of {WL.n_samples} samples x 1 EMCS, one sample per launch sequence"}
+
+
+def end_to_end(dev, cfg, J, seeds, steps):
+    """The user's path through the public API with host buffers: pinned host
+    couplings copied to the device at creation, reservoir pre-thermalisation,
+    `steps` EMCS each followed by a device-to-host read of the observables."""
+    import torch
+    from paper_2605_25872_gb300 import Batch
+    Jp = torch.from_numpy(J).pin_memory()
+    out = torch.empty((cfg.n_samples, cfg.n_temps, 8), dtype=torch.float64).pin_memory()
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    b = Batch(cfg, couplings=Jp, seeds=seeds, device=dev, stream=stream)
+    b.prethermalize(WL.res_pretherm_sweeps)
+    host = out.numpy()
+    for _ in range(steps):
+        b.emcs(1, graph=True)
+        b.read_observables(out=host)
+    stream.synchronize()
+    dt = time.perf_counter() - t0
+    pt, res = updates_per_emcs(cfg.n_samples)
+    pre = cfg.n_samples * WL.n_replicas * WL.n_res * WL.res_pretherm_sweeps * WL.V
+    b.close()
+    return {"value": (steps * (pt + res) + pre) / (dt * 1e9), "unit": UNIT,
+            "h2d_bytes_per_step": int((J.nbytes + seeds.nbytes) / steps),
+            "d2h_bytes_per_step": int(out.numel() * 8),
+            "includes": "H2D couplings+seeds, init, 960-sweep reservoir pre-thermalisation, "
+                        f"{steps} EMCS, D2H observables after every EMCS"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl != "reference":
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,258 @@
+/*
+ * pthr.h -- C ABI of the GB300 (sm_103a) PTHR hot path.
+ *
+ * PTHR (arXiv 2605.25872) is Parallel Tempering with all-cluster Houdayer
+ * moves and an entropic Reservoir, applied to the 3D Edwards-Anderson Ising
+ * spin glass with Gaussian couplings and periodic boundaries (Sec. 2,
+ * Eq. (1)).  One elementary Monte Carlo step (EMCS, Sec. 3) is
+ *   (i)   local sweeps of every clone at its temperature,     pthr_sweep
+ *   (ii)  the all-cluster update (ACU) of replica pairs, T<1, pthr_houdayer
+ *   (iii) the parallel-tempering (PT) exchange,               pthr_swap
+ *   (iv)  the entropic-reservoir (ER) exchange,               pthr_swap
+ * followed by a measurement,                                  pthr_observables.
+ *
+ * Conventions shared by every entry point:
+ *  - Plain pointers and sizes only.  "device" pointers are CUDA device (or
+ *    managed) memory of the current device; "host" pointers are CPU memory.
+ *  - The library allocates no device memory of its own: the caller allocates
+ *    one device workspace of pthr_required_bytes() bytes and keeps it alive
+ *    until pthr_destroy().  The library never frees it.
+ *  - Every call is asynchronous on the CUDA stream given at creation (or by
+ *    pthr_set_stream) and returns as soon as its kernels are enqueued.
+ *    Errors found on the host (bad arguments) return PTHR_E_INVAL at once;
+ *    CUDA launch errors return PTHR_E_CUDA; errors found on the device (a
+ *    bounded loop that hit its cap) are latched in a device status word and
+ *    returned by the next pthr_poll().
+ *  - Calls on one handle are not thread-safe; different handles are
+ *    independent.  pthr_last_error() describes the last failure.
+ *
+ * Geometry: site i = x + L*(y + L*z), 0 <= x,y,z < L, L even.  Couplings
+ * J[s][mu][i] (mu = 0,1,2 for x,y,z) belong to the bond (i, i + e_mu) of
+ * sample s.  Spins are +1/-1.  Temperatures T_k = t_min + k (t_max - t_min)
+ * / (n_temps - 1), k = 0..n_temps-1 (App. A.2).  Replica groups g =
+ * 0..n_replicas-1; the Houdayer pairs are (0,1), (2,3), ...  Each group owns
+ * n_temps + n_res storage lattices ("clones"); a permutation maps positions
+ * (temperature indices 0..n_temps-1, then reservoir slots) to clones.
+ * The local lattice index of clone c of group g is g*(n_temps+n_res) + c.
+ */
+#ifndef PTHR_H
+#define PTHR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define PTHR_API __attribute__((visibility("default")))
+#else
+#define PTHR_API
+#endif
+
+#define PTHR_MAX_L 24        /* largest supported linear size (shared-memory bound) */
+#define PTHR_NOBS 8          /* observable accumulators per (sample, temperature)   */
+
+typedef struct pthr_batch pthr_batch;   /* opaque handle; owns no device memory */
+
+typedef enum {
+    PTHR_OK = 0,
+    PTHR_E_INVAL = 1,        /* invalid argument or configuration                  */
+    PTHR_E_NOMEM = 2,        /* workspace smaller than pthr_required_bytes()       */
+    PTHR_E_CUDA = 3,         /* a CUDA runtime call or launch failed               */
+    PTHR_E_NOCONVERGE = 4,   /* a bounded device loop hit its iteration cap        */
+    PTHR_E_TIMEOUT = 5,      /* pthr_poll() timed out before the stream drained    */
+    PTHR_E_STATE = 6         /* call not valid now (e.g. during stream capture)    */
+} pthr_status;
+
+enum { PTHR_METROPOLIS = 0, PTHR_HEATBATH = 1 };
+enum { PTHR_CLUSTER_OFF = 0, PTHR_CLUSTER_ACU = 1, PTHR_CLUSTER_SINGLE = 2 };
+enum { PTHR_SWAP_PT = 1, PTHR_SWAP_ER = 2 };
+enum { PTHR_OBS_MEASURE = 1, PTHR_OBS_READ_HOST = 2, PTHR_OBS_READ_DEVICE = 4, PTHR_OBS_RESET = 8 };
+
+/* Workspace sub-buffers (pthr_buffer_info).  Layouts:
+ *  J      float    [S][3][V]        couplings, natural site order
+ *  SPINS  uint8    [S][n_lat][lat_bytes] internal packed layout (use
+ *                                   pthr_export_spins / pthr_import_spins)
+ *  ENERGY double   [S][n_lat]       energy of every clone (Eq. (1)), FP64
+ *  PERM   int32    [S][n_replicas][n_temps+n_res] position -> clone
+ *  AGE    uint32   [S][n_replicas][max(n_res,1)] EMCS spent in the reservoir
+ *  RT     uint8    [S][n_lat]       round-trip state (bit0 armed, bit1 saw T_min)
+ *  TRIPS  int64    [S][n_replicas]  completed round trips T_max->T_min->T_max
+ *  PTACC  int64    [S][n_replicas][n_temps] accepted exchanges of pair (k,k+1)
+ *  FLIPS  uint64   [S][n_lat]       accepted local moves
+ *  OBS    double   [S][n_temps][PTHR_NOBS] accumulators: count, sum e, sum e^2
+ *                                   (over groups), sum q, sum q^2, sum q_l,
+ *                                   sum S, sum q^4 (over pairs)
+ *  EMCS   uint32   [S]              EMCS counter of each sample
+ *  SEEDS  uint64   [S]              Philox key of each sample
+ *  ACTIVE uint8    [S]              0 = slot idle (skipped by every kernel)
+ *  STATUS uint32   [4]              device status word (error bits)
+ *  CSTAT  int64    [S][n_pairs][n_temps][4] cluster statistics of the last
+ *                                   cluster move: clusters, largest, second
+ *                                   largest, sites flipped
+ */
+enum {
+    PTHR_BUF_J = 0, PTHR_BUF_SPINS, PTHR_BUF_ENERGY, PTHR_BUF_PERM, PTHR_BUF_AGE,
+    PTHR_BUF_RT, PTHR_BUF_TRIPS, PTHR_BUF_PTACC, PTHR_BUF_FLIPS, PTHR_BUF_OBS,
+    PTHR_BUF_EMCS, PTHR_BUF_SEEDS, PTHR_BUF_ACTIVE, PTHR_BUF_STATUS, PTHR_BUF_CSTAT,
+    PTHR_NBUF
+};
+
+typedef struct {
+    int L;                    /* linear size: even, 2 <= L <= PTHR_MAX_L            */
+    int n_samples;            /* S >= 1 independent disorder samples                 */
+    int n_temps;              /* N_T >= 2 PT temperatures                            */
+    int n_replicas;           /* N_r >= 1 replica groups (even for cluster moves)    */
+    int n_res;                /* reservoir clones per group (paper: 4; 0 = none)     */
+    int sweeps_per_emcs;      /* local sweeps of PT clones per EMCS (paper: 10)      */
+    int res_sweeps_per_emcs;  /* sweeps of each reservoir clone per EMCS (960/4)     */
+    int acu_interval;         /* cluster move every acu_interval EMCS (>= 1)         */
+    int update_rule;          /* PTHR_METROPOLIS or PTHR_HEATBATH                    */
+    int cluster_mode;         /* PTHR_CLUSTER_OFF / _ACU / _SINGLE                   */
+    int er_on;                /* 1: entropic reservoir step on                       */
+    int reserved;             /* must be 0                                           */
+    double t_min, t_max;      /* temperature grid ends (t_max > t_min > 0)           */
+    double acu_t_below;       /* cluster moves only at T_k < acu_t_below (paper: 1)  */
+    uint64_t seed;            /* sample s uses Philox key seed + s unless seeds given */
+} pthr_config;
+
+/* Kernel shape knobs (autotuner).  0 = library default. */
+typedef struct {
+    int pt_lattices_per_block;    /* lattices of one sample per sweep block, PT      */
+    int res_lattices_per_block;   /* same for reservoir clones                       */
+    int sweep_threads;            /* threads per sweep block (multiple of the work)  */
+    int cluster_threads;          /* threads per cluster-move block                  */
+} pthr_tuning;
+
+/* Total workspace bytes for cfg (every sub-buffer 256-byte aligned).
+ * Returns PTHR_E_INVAL for an invalid cfg.  Host-only; no CUDA call. */
+PTHR_API pthr_status pthr_required_bytes(const pthr_config *cfg, size_t *bytes);
+
+/* Offset and size in bytes of workspace sub-buffer `buffer` (PTHR_BUF_*).
+ * Host-only; no CUDA call. */
+PTHR_API pthr_status pthr_buffer_info(const pthr_config *cfg, int buffer, size_t *offset,
+                                      size_t *bytes);
+
+/* Bytes of one lattice in the internal spin layout (for SPINS sizing). */
+PTHR_API pthr_status pthr_lattice_bytes(int L, size_t *bytes);
+
+/* Create a batch of cfg->n_samples samples in the caller-owned device
+ * workspace (>= pthr_required_bytes bytes, 256-byte aligned).
+ * couplings: host or device float [S][3][V] (copied), or NULL to draw them
+ *            on the device from each sample's seed (Sec. 2: J ~ N(0,1);
+ *            Box-Muller on Philox, rounded to multiples of 2^-18).
+ * seeds:     host uint64 [S] Philox keys, or NULL for cfg->seed + s.
+ * stream:    cudaStream_t (NULL = legacy default stream).
+ * Initialises hot-start spins (Sec. 3: random), identity permutations,
+ * reservoir ages 0..n_res-1, zero counters and every clone's energy.
+ * On success *out receives the handle.  Asynchronous. */
+PTHR_API pthr_status pthr_create_batch(const pthr_config *cfg, void *device_workspace,
+                                       size_t workspace_bytes, const float *couplings,
+                                       const uint64_t *seeds, void *stream, pthr_batch **out);
+
+/* Release the handle (not the workspace).  Safe on NULL. */
+PTHR_API void pthr_destroy(pthr_batch *b);
+
+/* Change the stream used by later calls. */
+PTHR_API pthr_status pthr_set_stream(pthr_batch *b, void *stream);
+
+/* Set kernel shape knobs (NULL restores defaults).  Results do not depend on
+ * them: every random number is keyed by (sample, lattice, site, step). */
+PTHR_API pthr_status pthr_set_tuning(pthr_batch *b, const pthr_tuning *t);
+PTHR_API pthr_status pthr_get_tuning(const pthr_batch *b, pthr_tuning *t);
+
+/* Step (i) of the EMCS (Sec. 3; App. A.1): n_pt_sweeps full-lattice
+ * checkerboard sweeps of every PT clone at its temperature and, at the same
+ * time, n_res_sweeps sweeps of every reservoir clone at T_max, with the
+ * configured update rule (Metropolis: flip iff Delta E <= 0 or
+ * u < exp(-Delta E / T); heat bath: s = +1 iff u < 1/(1 + exp(-2 h / T))),
+ * FP32 local fields, then every swept clone's energy in FP64.  Sweep
+ * indices continue within the current EMCS.  n_* >= 0; (0, 0) only
+ * recomputes energies. */
+PTHR_API pthr_status pthr_sweep(pthr_batch *b, int n_pt_sweeps, int n_res_sweeps);
+
+/* Step (ii) (Sec. 3, ACU): for each pair (2p, 2p+1) and each T_k <
+ * acu_t_below, the two clones at T_k: site overlaps q_i, clusters =
+ * connected components of {i ~ j : neighbours, q_i q_j > 0}, one random sign
+ * per cluster applied to both clones (PTHR_CLUSTER_ACU), or one q = -1
+ * cluster flipped (PTHR_CLUSTER_SINGLE), then both energies in FP64.  Runs
+ * only on EMCS whose index is a multiple of acu_interval. */
+PTHR_API pthr_status pthr_houdayer(pthr_batch *b);
+
+/* Canonical cluster labels (step (ii) without the flip) of every replica pair
+ * at every temperature: out_device int32 [S][n_replicas/2][n_temps][V]
+ * receives, for each site, the smallest site index of its cluster (the
+ * connected component of {i ~ j : neighbours, q_i q_j > 0}, Sec. 3).
+ * Diagnostic entry point; the spins are not changed. */
+PTHR_API pthr_status pthr_cluster_labels(pthr_batch *b, int32_t *out_device);
+
+/* Steps (iii) and (iv), then the end of the EMCS: PTHR_SWAP_PT runs one PT
+ * round per group (even pairs, then odd pairs; accept with
+ * min{1, exp((1/T_k - 1/T_{k+1})(E_k - E_{k+1}))}); PTHR_SWAP_ER exchanges
+ * the clone at T_max with the oldest reservoir clone (Sec. 3, ER).  Every
+ * call increments the EMCS counter of each active sample, whatever flags. */
+PTHR_API pthr_status pthr_swap(pthr_batch *b, int flags);
+
+/* Observables (Sec. 2, Eqs. (2)-(5)).  PTHR_OBS_MEASURE adds the current
+ * e = H/V, q, q^2, q_l, S = H/(3V) + (1 - q_l)/T and q^4 of every (sample,
+ * temperature) to the OBS accumulators; PTHR_OBS_READ_HOST (host out) or
+ * PTHR_OBS_READ_DEVICE (device out) copies the accumulators, double
+ * [S][n_temps][PTHR_NOBS], into out (bytes must be >= that size; a host
+ * read synchronises the stream); PTHR_OBS_RESET zeroes them afterwards. */
+PTHR_API pthr_status pthr_observables(pthr_batch *b, int flags, void *out, size_t bytes);
+
+/* n full EMCS: pthr_sweep(sweeps_per_emcs, er_on ? res_sweeps_per_emcs : 0),
+ * pthr_houdayer (if a cluster mode is set), pthr_swap(PT | ER if er_on),
+ * pthr_observables(MEASURE).  With use_graph = 1 one EMCS is captured into a
+ * CUDA graph on first use and replayed. */
+PTHR_API pthr_status pthr_emcs(pthr_batch *b, int n, int use_graph);
+
+/* n_sweeps sweeps at T_max of every reservoir clone before EMCS 0 (Sec. 3:
+ * the reservoir refreshes clones for 960 sweeps); uses EMCS counter word
+ * 0xFFFFFFFF.  Only the samples in [first, first+count). */
+PTHR_API pthr_status pthr_prethermalize_reservoir(pthr_batch *b, int first, int count,
+                                                  int n_sweeps);
+
+/* Wait up to timeout_ms (< 0: forever) for the stream to drain, then return
+ * the latched device status (PTHR_E_NOCONVERGE if a device loop hit its cap),
+ * or PTHR_E_TIMEOUT.  Clears the status word after reading it. */
+PTHR_API pthr_status pthr_poll(pthr_batch *b, int timeout_ms);
+
+/* Spins of every clone in natural order, int8 +1/-1, [S][n_lat][V], device
+ * memory (out / in).  Import also recomputes every energy. */
+PTHR_API pthr_status pthr_export_spins(pthr_batch *b, int8_t *out_device);
+PTHR_API pthr_status pthr_import_spins(pthr_batch *b, const int8_t *in_device);
+
+/* Serving: reinitialise samples [first, first+count) as new disorder
+ * samples (couplings host/device [count][3][V] or NULL = from seeds; seeds
+ * host [count], not NULL), EMCS counter 0, fresh spins, permutations, ages,
+ * counters and accumulators, optional reservoir pre-thermalisation, and mark
+ * them active.  Other samples are untouched (a request's result does not
+ * depend on its slot or neighbours). */
+PTHR_API pthr_status pthr_reset_samples(pthr_batch *b, int first, int count,
+                                        const float *couplings, const uint64_t *seeds,
+                                        int pretherm_sweeps);
+
+/* Mark samples [first, first+count) active (1) or idle (0). */
+PTHR_API pthr_status pthr_set_active(pthr_batch *b, int first, int count, int active);
+
+/* Checkpoint: the workspace holds the whole state (counter-based random
+ * numbers make resume exact), so a blob is the workspace plus a header.
+ * pthr_save with blob == NULL returns the size in *bytes; otherwise blob
+ * (host) receives it and the stream is synchronised.  pthr_load restores a
+ * blob saved from a batch with the same configuration. */
+PTHR_API pthr_status pthr_save(pthr_batch *b, void *blob, size_t *bytes);
+PTHR_API pthr_status pthr_load(pthr_batch *b, const void *blob, size_t bytes);
+
+/* Description of the last error on this handle (never NULL). */
+PTHR_API const char *pthr_last_error(const pthr_batch *b);
+
+/* Library version string. */
+PTHR_API const char *pthr_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PTHR_H */

@@ -1,0 +1,608 @@
+// capi.cu -- the extern "C" boundary declared in include/pthr.h: configuration
+// checks, workspace layout, launch shapes, EMCS schedule, CUDA-graph replay,
+// device-status polling and checkpoints.
+#include <chrono>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <thread>
+
+#include "kernels.cuh"
+
+using namespace pthr;
+
+struct pthr_batch {
+    pthr_config cfg;
+    Batch dev;
+    cudaStream_t stream;
+    pthr_tuning tuning;
+    void *ws;
+    size_t ws_bytes;
+    int pt_sweep_off, res_sweep_off;   // sweep index within the current EMCS
+    cudaGraph_t graph;
+    cudaGraphExec_t graph_exec;
+    int graph_ok;
+    char err[512];
+};
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+pthr_status fail(pthr_batch *b, pthr_status st, const char *fmt, ...) {
+    char *dst = b ? b->err : g_err;
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(dst, 512, fmt, ap);
+    va_end(ap);
+    return st;
+}
+
+pthr_status cuda_fail(pthr_batch *b, cudaError_t e, const char *what) {
+    return fail(b, PTHR_E_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CUDA_TRY(b, call, what)                         \
+    do {                                                \
+        cudaError_t e_ = (call);                        \
+        if (e_ != cudaSuccess) return cuda_fail((b), e_, (what)); \
+    } while (0)
+
+int n_pairs(const pthr_config *c) { return c->n_replicas / 2; }
+int n_slot(const pthr_config *c) { return c->n_temps + c->n_res; }
+int n_lat(const pthr_config *c) { return c->n_replicas * n_slot(c); }
+
+double host_temperature(const pthr_config *c, int k) {
+    Batch t{};
+    t.NT = c->n_temps;
+    t.t_min = c->t_min;
+    t.t_max = c->t_max;
+    return temperature(t, k);
+}
+
+int count_acu(const pthr_config *c) {
+    if (c->cluster_mode == PTHR_CLUSTER_OFF || c->n_replicas < 2) return 0;
+    int n = 0;
+    for (int k = 0; k < c->n_temps; ++k)
+        if (host_temperature(c, k) < c->acu_t_below) n = k + 1;
+    return n;
+}
+
+pthr_status check_config(const pthr_config *c) {
+    if (!c) return fail(nullptr, PTHR_E_INVAL, "config is NULL");
+    if (c->L < 2 || c->L > PTHR_MAX_L || (c->L & 1))
+        return fail(nullptr, PTHR_E_INVAL, "L must be even, 2 <= L <= %d (got %d)", PTHR_MAX_L, c->L);
+    if (c->n_samples < 1) return fail(nullptr, PTHR_E_INVAL, "n_samples must be >= 1");
+    if (c->n_temps < 2) return fail(nullptr, PTHR_E_INVAL, "n_temps must be >= 2");
+    if (c->n_replicas < 1 || c->n_replicas > 32)
+        return fail(nullptr, PTHR_E_INVAL, "n_replicas must be in [1, 32]");
+    if (c->n_res < 0) return fail(nullptr, PTHR_E_INVAL, "n_res must be >= 0");
+    if (n_slot(c) > 256) return fail(nullptr, PTHR_E_INVAL, "n_temps + n_res must be <= 256");
+    if (c->er_on && c->n_res < 1) return fail(nullptr, PTHR_E_INVAL, "er_on needs n_res >= 1");
+    if (c->sweeps_per_emcs < 0 || c->sweeps_per_emcs >= (1 << 22) || c->res_sweeps_per_emcs < 0 ||
+        c->res_sweeps_per_emcs >= (1 << 22))
+        return fail(nullptr, PTHR_E_INVAL, "sweeps per EMCS must be in [0, 2^22)");
+    if (c->acu_interval < 1) return fail(nullptr, PTHR_E_INVAL, "acu_interval must be >= 1");
+    if (c->update_rule != PTHR_METROPOLIS && c->update_rule != PTHR_HEATBATH)
+        return fail(nullptr, PTHR_E_INVAL, "unknown update_rule %d", c->update_rule);
+    if (c->cluster_mode < PTHR_CLUSTER_OFF || c->cluster_mode > PTHR_CLUSTER_SINGLE)
+        return fail(nullptr, PTHR_E_INVAL, "unknown cluster_mode %d", c->cluster_mode);
+    if (c->cluster_mode != PTHR_CLUSTER_OFF && (c->n_replicas < 2 || (c->n_replicas & 1)))
+        return fail(nullptr, PTHR_E_INVAL, "cluster moves need an even n_replicas >= 2");
+    if (!(c->t_min > 0.0) || !(c->t_max > c->t_min))
+        return fail(nullptr, PTHR_E_INVAL, "need 0 < t_min < t_max");
+    if (c->reserved != 0) return fail(nullptr, PTHR_E_INVAL, "reserved must be 0");
+    return PTHR_OK;
+}
+
+struct Layout {
+    size_t off[PTHR_NBUF];
+    size_t len[PTHR_NBUF];
+    size_t total;
+};
+
+Layout make_layout(const pthr_config *c) {
+    const size_t S = (size_t)c->n_samples, V = (size_t)c->L * c->L * c->L;
+    const size_t NL = (size_t)n_lat(c), NR = (size_t)c->n_replicas, NT = (size_t)c->n_temps;
+    const size_t NRES = (size_t)(c->n_res > 0 ? c->n_res : 1);
+    const size_t NP = (size_t)(n_pairs(c) > 0 ? n_pairs(c) : 1);
+    Layout l{};
+    l.len[PTHR_BUF_J] = S * 3 * V * sizeof(float);
+    l.len[PTHR_BUF_SPINS] = S * NL * (size_t)lattice_words(c->L) * 4;
+    l.len[PTHR_BUF_ENERGY] = S * NL * sizeof(double);
+    l.len[PTHR_BUF_PERM] = S * NR * (size_t)n_slot(c) * sizeof(int32_t);
+    l.len[PTHR_BUF_AGE] = S * NR * NRES * sizeof(uint32_t);
+    l.len[PTHR_BUF_RT] = S * NL;
+    l.len[PTHR_BUF_TRIPS] = S * NR * sizeof(long long);
+    l.len[PTHR_BUF_PTACC] = S * NR * NT * sizeof(long long);
+    l.len[PTHR_BUF_FLIPS] = S * NL * sizeof(unsigned long long);
+    l.len[PTHR_BUF_OBS] = S * NT * PTHR_NOBS * sizeof(double);
+    l.len[PTHR_BUF_EMCS] = S * sizeof(uint32_t);
+    l.len[PTHR_BUF_SEEDS] = S * sizeof(unsigned long long);
+    l.len[PTHR_BUF_ACTIVE] = S;
+    l.len[PTHR_BUF_STATUS] = 4 * sizeof(uint32_t);
+    l.len[PTHR_BUF_CSTAT] = S * NP * NT * 4 * sizeof(long long);
+    size_t o = 0;
+    for (int i = 0; i < PTHR_NBUF; ++i) {
+        l.off[i] = o;
+        o += (l.len[i] + 255) & ~(size_t)255;
+    }
+    l.total = o;
+    return l;
+}
+
+// Kernel shapes.  Sweep: lattices per block K (PT / reservoir), groups per
+// lattice lane Gt (divides G, <= 512), threads = P * Gt.
+struct SweepShape { int K_pt, K_res, Gt, threads, pt_tasks, res_tasks; };
+
+int default_k(const pthr_config *c, int total_entries) {
+    const size_t lb = (size_t)lattice_words(c->L) * 4;
+    const size_t budget = 220 * 1024;
+    long k = (long)((budget - 12 * lb) / lb);
+    if (c->L == 16) k = 16;             // two blocks per SM
+    if (k > sweep_max_k()) k = sweep_max_k();
+    if (k < 1) k = 1;
+    if (k > total_entries) k = total_entries;
+    return (int)k;
+}
+
+SweepShape sweep_shape(const pthr_batch *b) {
+    const pthr_config *c = &b->cfg;
+    SweepShape sh{};
+    const int npt = c->n_replicas * c->n_temps;
+    const int nres = c->n_replicas * (c->n_res > 0 ? c->n_res : 1);
+    sh.K_pt = b->tuning.pt_lattices_per_block > 0 ? b->tuning.pt_lattices_per_block : default_k(c, npt);
+    sh.K_res = b->tuning.res_lattices_per_block > 0 ? b->tuning.res_lattices_per_block : default_k(c, nres);
+    if (sh.K_pt > npt) sh.K_pt = npt;
+    if (sh.K_res > nres) sh.K_res = nres;
+    const int G = sweep_groups_for(c->L);
+    int Gt = G;
+    if (G > 512) {
+        for (int d = 2; d <= G; ++d)
+            if (G % d == 0 && G / d <= 512) { Gt = G / d; break; }
+    }
+    sh.Gt = Gt;
+    const int Kmax = sh.K_pt > sh.K_res ? sh.K_pt : sh.K_res;
+    int P = 512 / Gt;
+    if (b->tuning.sweep_threads > 0) P = b->tuning.sweep_threads / Gt;
+    if (P < 1) P = 1;
+    if (P > Kmax) P = Kmax;
+    sh.threads = P * Gt;
+    sh.pt_tasks = (npt + sh.K_pt - 1) / sh.K_pt;
+    sh.res_tasks = (nres + sh.K_res - 1) / sh.K_res;
+    return sh;
+}
+
+pthr_status do_sweep(pthr_batch *b, int n_pt, int n_res, int first, int count, int pretherm) {
+    const pthr_config *c = &b->cfg;
+    SweepShape sh = sweep_shape(b);
+    SweepArgs a{};
+    a.b = b->dev;
+    a.n_pt_sweeps = n_pt;
+    a.n_res_sweeps = n_res;
+    a.pt_sweep_base = pretherm ? 0 : b->pt_sweep_off;
+    a.res_sweep_base = pretherm ? 0 : b->res_sweep_off;
+    a.K_pt = sh.K_pt;
+    a.K_res = sh.K_res;
+    a.pt_tasks = sh.pt_tasks;
+    a.res_tasks = sh.res_tasks;
+    a.do_pt = pretherm ? 0 : ((n_pt > 0 || n_res == 0) ? 1 : 0);
+    a.do_res = (c->n_res > 0 && (n_res > 0 || n_pt == 0)) ? 1 : 0;
+    a.sample_first = first;
+    a.sample_count = count;
+    a.emcs_override = pretherm;
+    a.Gt = sh.Gt;
+    const int blocks = count * ((a.do_res ? sh.res_tasks : 0) + (a.do_pt ? sh.pt_tasks : 0));
+    if (blocks == 0) return PTHR_OK;
+    const size_t smem = sweep_smem_bytes_for(c->L, sh.K_pt > sh.K_res ? sh.K_pt : sh.K_res);
+    if (smem > 220 * 1024)
+        return fail(b, PTHR_E_INVAL, "sweep block needs %zu bytes of shared memory; lower the lattices per block", smem);
+    CUDA_TRY(b, launch_sweep(a, blocks, sh.threads, b->stream), "sweep launch");
+    return PTHR_OK;
+}
+
+pthr_status do_cluster(pthr_batch *b, int label_only, int32_t *labels) {
+    if (b->dev.n_acu == 0 && !label_only) return PTHR_OK;
+    ClusterArgs a{};
+    a.b = b->dev;
+    if (label_only) {   // label every temperature
+        a.b.n_acu = b->cfg.n_temps;
+        if (b->dev.NPAIR == 0) return fail(b, PTHR_E_INVAL, "no replica pairs");
+    }
+    a.sample_first = 0;
+    a.sample_count = b->cfg.n_samples;
+    a.label_only = label_only;
+    a.labels_out = labels;
+    int threads = b->tuning.cluster_threads > 0 ? b->tuning.cluster_threads : 512;
+    const int V = b->cfg.L * b->cfg.L * b->cfg.L;
+    if (threads > ((V + 31) / 32) * 32) threads = ((V + 31) / 32) * 32;
+    if (threads < 32) threads = 32;
+    threads = (threads / 32) * 32;
+    if (cluster_smem_bytes_for(b->cfg.L) > 200 * 1024)
+        return fail(b, PTHR_E_INVAL, "cluster block does not fit in shared memory");
+    CUDA_TRY(b, launch_cluster(a, threads, b->stream), "cluster launch");
+    return PTHR_OK;
+}
+
+pthr_status one_emcs(pthr_batch *b) {
+    const pthr_config *c = &b->cfg;
+    pthr_status st = do_sweep(b, c->sweeps_per_emcs, c->er_on ? c->res_sweeps_per_emcs : 0, 0,
+                              c->n_samples, 0);
+    if (st != PTHR_OK) return st;
+    if (c->cluster_mode != PTHR_CLUSTER_OFF) {
+        st = do_cluster(b, 0, nullptr);
+        if (st != PTHR_OK) return st;
+    }
+    CUDA_TRY(b, launch_swap(b->dev, PTHR_SWAP_PT | (c->er_on ? PTHR_SWAP_ER : 0), 0, c->n_samples,
+                            b->stream), "swap launch");
+    CUDA_TRY(b, launch_measure(b->dev, 0, c->n_samples, b->stream), "measure launch");
+    return PTHR_OK;
+}
+
+bool capturing(cudaStream_t s) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) return false;
+    return cs != cudaStreamCaptureStatusNone;
+}
+
+}  // namespace
+
+extern "C" {
+
+PTHR_API const char *pthr_version(void) { return "pthr-gb300 0.1 (sm_103a)"; }
+
+PTHR_API pthr_status pthr_required_bytes(const pthr_config *cfg, size_t *bytes) {
+    pthr_status st = check_config(cfg);
+    if (st != PTHR_OK) return st;
+    if (!bytes) return fail(nullptr, PTHR_E_INVAL, "bytes is NULL");
+    *bytes = make_layout(cfg).total;
+    return PTHR_OK;
+}
+
+PTHR_API pthr_status pthr_buffer_info(const pthr_config *cfg, int buffer, size_t *offset, size_t *bytes) {
+    pthr_status st = check_config(cfg);
+    if (st != PTHR_OK) return st;
+    if (buffer < 0 || buffer >= PTHR_NBUF || !offset || !bytes)
+        return fail(nullptr, PTHR_E_INVAL, "bad buffer id or NULL output");
+    Layout l = make_layout(cfg);
+    *offset = l.off[buffer];
+    *bytes = l.len[buffer];
+    return PTHR_OK;
+}
+
+PTHR_API pthr_status pthr_lattice_bytes(int L, size_t *bytes) {
+    if (L < 2 || L > PTHR_MAX_L || (L & 1) || !bytes) return fail(nullptr, PTHR_E_INVAL, "bad L");
+    *bytes = (size_t)lattice_words(L) * 4;
+    return PTHR_OK;
+}
+
+PTHR_API pthr_status pthr_create_batch(const pthr_config *cfg, void *device_workspace, size_t workspace_bytes,
+                                       const float *couplings, const uint64_t *seeds, void *stream,
+                                       pthr_batch **out) {
+    pthr_status st = check_config(cfg);
+    if (st != PTHR_OK) return st;
+    if (!out) return fail(nullptr, PTHR_E_INVAL, "out is NULL");
+    *out = nullptr;
+    if (!device_workspace) return fail(nullptr, PTHR_E_INVAL, "workspace is NULL");
+    if (((uintptr_t)device_workspace) & 255) return fail(nullptr, PTHR_E_INVAL, "workspace must be 256-byte aligned");
+    Layout l = make_layout(cfg);
+    if (workspace_bytes < l.total)
+        return fail(nullptr, PTHR_E_NOMEM, "workspace has %zu bytes, needs %zu", workspace_bytes, l.total);
+    pthr_batch *b = new pthr_batch();
+    memset(b->err, 0, sizeof(b->err));
+    b->cfg = *cfg;
+    b->stream = (cudaStream_t)stream;
+    b->ws = device_workspace;
+    b->ws_bytes = workspace_bytes;
+    unsigned char *base = (unsigned char *)device_workspace;
+    Batch &d = b->dev;
+    d.J = (float *)(base + l.off[PTHR_BUF_J]);
+    d.spins = (uint32_t *)(base + l.off[PTHR_BUF_SPINS]);
+    d.E = (double *)(base + l.off[PTHR_BUF_ENERGY]);
+    d.perm = (int32_t *)(base + l.off[PTHR_BUF_PERM]);
+    d.age = (uint32_t *)(base + l.off[PTHR_BUF_AGE]);
+    d.rt = (uint8_t *)(base + l.off[PTHR_BUF_RT]);
+    d.trips = (long long *)(base + l.off[PTHR_BUF_TRIPS]);
+    d.ptacc = (long long *)(base + l.off[PTHR_BUF_PTACC]);
+    d.flips = (unsigned long long *)(base + l.off[PTHR_BUF_FLIPS]);
+    d.obs = (double *)(base + l.off[PTHR_BUF_OBS]);
+    d.emcs = (uint32_t *)(base + l.off[PTHR_BUF_EMCS]);
+    d.seeds = (unsigned long long *)(base + l.off[PTHR_BUF_SEEDS]);
+    d.active = (uint8_t *)(base + l.off[PTHR_BUF_ACTIVE]);
+    d.status = (uint32_t *)(base + l.off[PTHR_BUF_STATUS]);
+    d.cstat = (long long *)(base + l.off[PTHR_BUF_CSTAT]);
+    d.S = cfg->n_samples;
+    d.L = cfg->L;
+    d.NT = cfg->n_temps;
+    d.NR = cfg->n_replicas;
+    d.NRES = cfg->n_res;
+    d.NSLOT = n_slot(cfg);
+    d.NLAT = n_lat(cfg);
+    d.NPAIR = n_pairs(cfg);
+    d.lat_words = lattice_words(cfg->L);
+    d.rule = cfg->update_rule;
+    d.cluster_mode = cfg->cluster_mode;
+    d.acu_interval = cfg->acu_interval;
+    d.n_acu = count_acu(cfg);
+    d.t_min = cfg->t_min;
+    d.t_max = cfg->t_max;
+
+    // seeds (host), status word
+    unsigned long long *hs = new unsigned long long[cfg->n_samples];
+    for (int s = 0; s < cfg->n_samples; ++s) hs[s] = seeds ? seeds[s] : cfg->seed + (unsigned long long)s;
+    cudaError_t e = cudaMemcpyAsync(d.seeds, hs, sizeof(unsigned long long) * cfg->n_samples,
+                                    cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);   // hs is pageable and freed below
+    delete[] hs;
+    if (e == cudaSuccess) e = cudaMemsetAsync(d.status, 0, 16, b->stream);
+    if (e != cudaSuccess) { pthr_status r = cuda_fail(nullptr, e, "create"); delete b; return r; }
+    if (couplings) {
+        e = cudaMemcpyAsync(d.J, couplings, l.len[PTHR_BUF_J], cudaMemcpyDefault, b->stream);
+    } else {
+        e = launch_couplings_from_seed(d, 0, cfg->n_samples, b->stream);
+    }
+    if (e == cudaSuccess) e = launch_init_state(d, 0, cfg->n_samples, b->stream);
+    if (e != cudaSuccess) { pthr_status r = cuda_fail(nullptr, e, "create/init"); delete b; return r; }
+    st = do_sweep(b, 0, 0, 0, cfg->n_samples, 0);   // energies of every clone
+    if (st != PTHR_OK) { fail(nullptr, st, "%s", b->err); delete b; return st; }
+    *out = b;
+    return PTHR_OK;
+}
+
+PTHR_API void pthr_destroy(pthr_batch *b) {
+    if (!b) return;
+    if (b->graph_exec) cudaGraphExecDestroy(b->graph_exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    delete b;
+}
+
+PTHR_API pthr_status pthr_set_stream(pthr_batch *b, void *stream) {
+    if (!b) return fail(nullptr, PTHR_E_INVAL, "NULL handle");
+    b->stream = (cudaStream_t)stream;
+    return PTHR_OK;
+}
+
+PTHR_API pthr_status pthr_set_tuning(pthr_batch *b, const pthr_tuning *t) {
+    if (!b) return fail(nullptr, PTHR_E_INVAL, "NULL handle");
+    pthr_tuning nt{};
+    if (t) nt = *t;
+    if (nt.pt_lattices_per_block < 0 || nt.pt_lattices_per_block > sweep_max_k() ||
+        nt.res_lattices_per_block < 0 || nt.res_lattices_per_block > sweep_max_k() ||
+        nt.sweep_threads < 0 || nt.sweep_threads > 512 || nt.cluster_threads < 0 || nt.cluster_threads > 1024)
+        return fail(b, PTHR_E_INVAL, "tuning out of range");
+    pthr_tuning old = b->tuning;
+    b->tuning = nt;
+    SweepShape sh = sweep_shape(b);
+    const size_t smem = sweep_smem_bytes_for(b->cfg.L, sh.K_pt > sh.K_res ? sh.K_pt : sh.K_res);
+    if (smem > 220 * 1024) {
+        b->tuning = old;
+        return fail(b, PTHR_E_INVAL, "tuning needs %zu bytes of shared memory per block", smem);
+    }
+    if (b->graph_exec) { cudaGraphExecDestroy(b->graph_exec); b->graph_exec = nullptr; }
+    if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
+    b->graph_ok = 0;
+    return PTHR_OK;
+}
+
+PTHR_API pthr_status pthr_get_tuning(const pthr_batch *b, pthr_tuning *t) {
+    if (!b || !t) return fail(nullptr, PTHR_E_INVAL, "NULL argument");
+    SweepShape sh = sweep_shape(b);
+    t->pt_lattices_per_block = sh.K_pt;
+    t->res_lattices_per_block = sh.K_res;
+    t->sweep_threads = sh.threads;
+    t->cluster_threads = b->tuning.cluster_threads > 0 ? b->tuning.cluster_threads : 512;
+    return PTHR_OK;
+}
+
+PTHR_API pthr_status pthr_sweep(pthr_batch *b, int n_pt_sweeps, int n_res_sweeps) {
+    if (!b) return fail(nullptr, PTHR_E_INVAL, "NULL handle");
+    if (n_pt_sweeps < 0 || n_res_sweeps < 0) return fail(b, PTHR_E_INVAL, "negative sweep count");
+    if ((long)b->pt_sweep_off + n_pt_sweeps >= (1L << 23) || (long)b->res_sweep_off + n_res_sweeps >= (1L << 23))
+        return fail(b, PTHR_E_INVAL, "more than 2^23 sweeps in one EMCS");
+    if (n_res_sweeps > 0 && b->cfg.n_res == 0) n_res_sweeps = 0;
+    pthr_status st = do_sweep(b, n_pt_sweeps, n_res_sweeps, 0, b->cfg.n_samples, 0);
+    if (st != PTHR_OK) return st;
+    b->pt_sweep_off += n_pt_sweeps;
+    b->res_sweep_off += n_res_sweeps;
+    return PTHR_OK;
+}
+
+PTHR_API pthr_status pthr_houdayer(pthr_batch *b) {
+    if (!b) return fail(nullptr, PTHR_E_INVAL, "NULL handle");
+    if (b->cfg.cluster_mode == PTHR_CLUSTER_OFF) return PTHR_OK;
+    return do_cluster(b, 0, nullptr);
+}
+
+PTHR_API pthr_status pthr_cluster_labels(pthr_batch *b, int32_t *out_device) {
+    if (!b || !out_device) return fail(b, PTHR_E_INVAL, "NULL argument");
+    return do_cluster(b, 1, out_device);
+}
+
+PTHR_API pthr_status pthr_swap(pthr_batch *b, int flags) {
+    if (!b) return fail(nullptr, PTHR_E_INVAL, "NULL handle");
+    if (flags & ~(PTHR_SWAP_PT | PTHR_SWAP_ER)) return fail(b, PTHR_E_INVAL, "unknown swap flags");
+    if ((flags & PTHR_SWAP_ER) && b->cfg.n_res < 1) return fail(b, PTHR_E_INVAL, "ER needs n_res >= 1");
+    CUDA_TRY(b, launch_swap(b->dev, flags, 0, b->cfg.n_samples, b->stream), "swap launch");
+    b->pt_sweep_off = 0;
+    b->res_sweep_off = 0;
+    return PTHR_OK;
+}
+
+PTHR_API pthr_status pthr_observables(pthr_batch *b, int flags, void *out, size_t bytes) {
+    if (!b) return fail(nullptr, PTHR_E_INVAL, "NULL handle");
+    const size_t need = (size_t)b->cfg.n_samples * b->cfg.n_temps * PTHR_NOBS * sizeof(double);
+    if ((flags & (PTHR_OBS_READ_HOST | PTHR_OBS_READ_DEVICE)) && (!out || bytes < need))
+        return fail(b, PTHR_E_INVAL, "output buffer needs %zu bytes", need);
+    if (flags & PTHR_OBS_MEASURE)
+        CUDA_TRY(b, launch_measure(b->dev, 0, b->cfg.n_samples, b->stream), "measure launch");
+    if (flags & PTHR_OBS_READ_DEVICE)
+        CUDA_TRY(b, cudaMemcpyAsync(out, b->dev.obs, need, cudaMemcpyDeviceToDevice, b->stream), "obs copy");
+    if (flags & PTHR_OBS_READ_HOST) {
+        CUDA_TRY(b, cudaMemcpyAsync(out, b->dev.obs, need, cudaMemcpyDeviceToHost, b->stream), "obs copy");
+        CUDA_TRY(b, cudaStreamSynchronize(b->stream), "obs sync");
+    }
+    if (flags & PTHR_OBS_RESET)
+        CUDA_TRY(b, cudaMemsetAsync(b->dev.obs, 0, need, b->stream), "obs reset");
+    return PTHR_OK;
+}
+
+PTHR_API pthr_status pthr_emcs(pthr_batch *b, int n, int use_graph) {
+    if (!b) return fail(nullptr, PTHR_E_INVAL, "NULL handle");
+    if (n < 0) return fail(b, PTHR_E_INVAL, "negative EMCS count");
+    if (b->pt_sweep_off || b->res_sweep_off)
+        return fail(b, PTHR_E_STATE, "pthr_emcs must start at an EMCS boundary (call pthr_swap first)");
+    if (use_graph && b->stream != nullptr && !capturing(b->stream)) {
+        if (!b->graph_ok) {
+            CUDA_TRY(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+            pthr_status st = one_emcs(b);
+            cudaGraph_t g = nullptr;
+            cudaError_t e = cudaStreamEndCapture(b->stream, &g);
+            if (st != PTHR_OK) { if (g) cudaGraphDestroy(g); return st; }
+            if (e != cudaSuccess) return cuda_fail(b, e, "end capture");
+            cudaGraphExec_t ge = nullptr;
+            e = cudaGraphInstantiate(&ge, g, 0);
+            if (e != cudaSuccess) { cudaGraphDestroy(g); return cuda_fail(b, e, "graph instantiate"); }
+            b->graph = g;
+            b->graph_exec = ge;
+            b->graph_ok = 1;
+        }
+        for (int i = 0; i < n; ++i) CUDA_TRY(b, cudaGraphLaunch(b->graph_exec, b->stream), "graph launch");
+        return PTHR_OK;
+    }
+    for (int i = 0; i < n; ++i) {
+        pthr_status st = one_emcs(b);
+        if (st != PTHR_OK) return st;
+    }
+    return PTHR_OK;
+}
+
+PTHR_API pthr_status pthr_prethermalize_reservoir(pthr_batch *b, int first, int count, int n_sweeps) {
+    if (!b) return fail(nullptr, PTHR_E_INVAL, "NULL handle");
+    if (first < 0 || count < 0 || first + count > b->cfg.n_samples || n_sweeps < 0 || n_sweeps >= (1 << 23))
+        return fail(b, PTHR_E_INVAL, "bad sample range or sweep count");
+    if (b->cfg.n_res == 0 || n_sweeps == 0 || count == 0) return PTHR_OK;
+    return do_sweep(b, 0, n_sweeps, first, count, 1);
+}
+
+PTHR_API pthr_status pthr_poll(pthr_batch *b, int timeout_ms) {
+    if (!b) return fail(nullptr, PTHR_E_INVAL, "NULL handle");
+    cudaEvent_t ev;
+    CUDA_TRY(b, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "event create");
+    cudaError_t e = cudaEventRecord(ev, b->stream);
+    if (e != cudaSuccess) { cudaEventDestroy(ev); return cuda_fail(b, e, "event record"); }
+    auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        e = cudaEventQuery(ev);
+        if (e == cudaSuccess) break;
+        if (e != cudaErrorNotReady) { cudaEventDestroy(ev); return cuda_fail(b, e, "stream"); }
+        if (timeout_ms >= 0) {
+            auto ms = std::chrono::duration_cast<std::chrono::milliseconds>(std::chrono::steady_clock::now() - t0).count();
+            if (ms > timeout_ms) { cudaEventDestroy(ev); return fail(b, PTHR_E_TIMEOUT, "stream still busy after %d ms", timeout_ms); }
+        }
+        std::this_thread::sleep_for(std::chrono::microseconds(200));
+    }
+    cudaEventDestroy(ev);
+    uint32_t st[4] = {0, 0, 0, 0};
+    CUDA_TRY(b, cudaMemcpy(st, b->dev.status, sizeof(st), cudaMemcpyDeviceToHost), "status read");
+    CUDA_TRY(b, cudaMemset(b->dev.status, 0, sizeof(st)), "status clear");
+    if (st[0] & STATUS_NOCONVERGE) return fail(b, PTHR_E_NOCONVERGE, "a cluster labelling loop hit its iteration cap");
+    if (st[0] & STATUS_BOUNDS) return fail(b, PTHR_E_NOCONVERGE, "a device bounds check failed");
+    return PTHR_OK;
+}
+
+PTHR_API pthr_status pthr_export_spins(pthr_batch *b, int8_t *out_device) {
+    if (!b || !out_device) return fail(b, PTHR_E_INVAL, "NULL argument");
+    CUDA_TRY(b, launch_export_spins(b->dev, out_device, b->stream), "export launch");
+    return PTHR_OK;
+}
+
+PTHR_API pthr_status pthr_import_spins(pthr_batch *b, const int8_t *in_device) {
+    if (!b || !in_device) return fail(b, PTHR_E_INVAL, "NULL argument");
+    CUDA_TRY(b, launch_import_spins(b->dev, in_device, b->stream), "import launch");
+    return do_sweep(b, 0, 0, 0, b->cfg.n_samples, 0);
+}
+
+PTHR_API pthr_status pthr_reset_samples(pthr_batch *b, int first, int count, const float *couplings,
+                                        const uint64_t *seeds, int pretherm_sweeps) {
+    if (!b) return fail(nullptr, PTHR_E_INVAL, "NULL handle");
+    if (first < 0 || count < 1 || first + count > b->cfg.n_samples || !seeds || pretherm_sweeps < 0)
+        return fail(b, PTHR_E_INVAL, "bad sample range, seeds or pre-thermalisation");
+    if (b->pt_sweep_off || b->res_sweep_off)
+        return fail(b, PTHR_E_STATE, "samples can only be reset at an EMCS boundary");
+    const Batch &d = b->dev;
+    const size_t V = (size_t)d.L * d.L * d.L;
+    CUDA_TRY(b, cudaMemcpyAsync(d.seeds + first, seeds, sizeof(unsigned long long) * count,
+                                cudaMemcpyDefault, b->stream), "seed copy");
+    // seeds may be pageable host memory: make the copy complete before returning
+    CUDA_TRY(b, cudaStreamSynchronize(b->stream), "seed copy sync");
+    if (couplings)
+        CUDA_TRY(b, cudaMemcpyAsync(d.J + (size_t)first * 3 * V, couplings, sizeof(float) * 3 * V * count,
+                                    cudaMemcpyDefault, b->stream), "coupling copy");
+    else
+        CUDA_TRY(b, launch_couplings_from_seed(d, first, count, b->stream), "couplings");
+    CUDA_TRY(b, launch_init_state(d, first, count, b->stream), "init");
+    pthr_status st = do_sweep(b, 0, 0, first, count, 0);
+    if (st != PTHR_OK) return st;
+    if (pretherm_sweeps > 0 && b->cfg.n_res > 0) {
+        st = do_sweep(b, 0, pretherm_sweeps, first, count, 1);
+        if (st != PTHR_OK) return st;
+    }
+    return PTHR_OK;
+}
+
+PTHR_API pthr_status pthr_set_active(pthr_batch *b, int first, int count, int active) {
+    if (!b) return fail(nullptr, PTHR_E_INVAL, "NULL handle");
+    if (first < 0 || count < 0 || first + count > b->cfg.n_samples) return fail(b, PTHR_E_INVAL, "bad sample range");
+    if (count == 0) return PTHR_OK;
+    CUDA_TRY(b, cudaMemsetAsync(b->dev.active + first, active ? 1 : 0, count, b->stream), "set active");
+    return PTHR_OK;
+}
+
+struct BlobHeader {
+    char magic[8];
+    uint32_t version;
+    uint32_t pad;
+    pthr_config cfg;
+    int32_t pt_sweep_off, res_sweep_off;
+    uint64_t ws_bytes;
+};
+
+PTHR_API pthr_status pthr_save(pthr_batch *b, void *blob, size_t *bytes) {
+    if (!b || !bytes) return fail(b, PTHR_E_INVAL, "NULL argument");
+    const size_t total = make_layout(&b->cfg).total;
+    const size_t need = sizeof(BlobHeader) + total;
+    if (!blob) { *bytes = need; return PTHR_OK; }
+    if (*bytes < need) return fail(b, PTHR_E_INVAL, "blob needs %zu bytes", need);
+    BlobHeader h{};
+    memcpy(h.magic, "PTHRBLOB", 8);
+    h.version = 1;
+    h.cfg = b->cfg;
+    h.pt_sweep_off = b->pt_sweep_off;
+    h.res_sweep_off = b->res_sweep_off;
+    h.ws_bytes = total;
+    memcpy(blob, &h, sizeof(h));
+    CUDA_TRY(b, cudaMemcpyAsync((unsigned char *)blob + sizeof(h), b->ws, total, cudaMemcpyDeviceToHost, b->stream), "save copy");
+    CUDA_TRY(b, cudaStreamSynchronize(b->stream), "save sync");
+    *bytes = need;
+    return PTHR_OK;
+}
+
+PTHR_API pthr_status pthr_load(pthr_batch *b, const void *blob, size_t bytes) {
+    if (!b || !blob) return fail(b, PTHR_E_INVAL, "NULL argument");
+    BlobHeader h;
+    if (bytes < sizeof(h)) return fail(b, PTHR_E_INVAL, "blob too small");
+    memcpy(&h, blob, sizeof(h));
+    const size_t total = make_layout(&b->cfg).total;
+    if (memcmp(h.magic, "PTHRBLOB", 8) != 0 || h.version != 1) return fail(b, PTHR_E_INVAL, "not a pthr blob");
+    if (memcmp(&h.cfg, &b->cfg, sizeof(pthr_config)) != 0 || h.ws_bytes != total || bytes < sizeof(h) + total)
+        return fail(b, PTHR_E_INVAL, "blob was saved from a different configuration");
+    CUDA_TRY(b, cudaMemcpyAsync(b->ws, (const unsigned char *)blob + sizeof(h), total, cudaMemcpyHostToDevice, b->stream), "load copy");
+    CUDA_TRY(b, cudaStreamSynchronize(b->stream), "load sync");
+    b->pt_sweep_off = h.pt_sweep_off;
+    b->res_sweep_off = h.res_sweep_off;
+    return PTHR_OK;
+}
+
+PTHR_API const char *pthr_last_error(const pthr_batch *b) { return b ? b->err : g_err; }
+
+}  // extern "C"

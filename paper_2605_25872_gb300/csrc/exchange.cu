@@ -1,0 +1,173 @@
+// exchange.cu -- steps (iii) and (iv) of the EMCS (Sec. 3: PT and ER) and the
+// measurement of the observables (Sec. 2, Eqs. (2)-(5)).
+//
+// swap_kernel: one block per sample, one warp per replica group.  The warp
+// holds its group's permutation and energies in shared memory, runs the even
+// then the odd phase of the PT round (disjoint pairs, one lane each), marks
+// the clone that reached T_min, exchanges the clone at T_max with the oldest
+// reservoir clone, and finally the block advances the sample's EMCS counter.
+#include "kernels.cuh"
+
+namespace pthr {
+
+namespace {
+
+constexpr int MAX_SLOT = 256;
+
+__global__ void swap_kernel(Batch b, int flags, int first) {
+    const int s = first + blockIdx.x;
+    if (!b.active[s]) return;
+    const int g = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    extern __shared__ __align__(16) unsigned char smem[];
+    double *s_E = reinterpret_cast<double *>(smem);                    // [NR][NSLOT]
+    int *s_perm = reinterpret_cast<int *>(s_E + b.NR * b.NSLOT);       // [NR][NSLOT]
+    const uint32_t emcs = b.emcs[s];
+    const unsigned long long seed = b.seeds[s];
+    if (g < b.NR) {
+        int *perm = s_perm + g * b.NSLOT;
+        double *Ep = s_E + g * b.NSLOT;
+        int32_t *gperm = b.perm + ((size_t)s * b.NR + g) * b.NSLOT;
+        for (int i = lane; i < b.NSLOT; i += 32) perm[i] = gperm[i];
+        __syncwarp();
+        for (int i = lane; i < b.NT; i += 32) Ep[i] = b.E[(size_t)s * b.NLAT + g * b.NSLOT + perm[i]];
+        __syncwarp();
+        if (flags & PTHR_SWAP_PT) {
+            long long *acc = b.ptacc + ((size_t)s * b.NR + g) * b.NT;
+            for (int ph = 0; ph < 2; ++ph) {
+                for (int k = ph + 2 * lane; k + 1 < b.NT; k += 64) {
+                    const double bk = __ddiv_rn(1.0, temperature(b, k));
+                    const double bk1 = __ddiv_rn(1.0, temperature(b, k + 1));
+                    const double delta = __dmul_rn(__dsub_rn(bk, bk1), __dsub_rn(Ep[k], Ep[k + 1]));
+                    bool accept = delta >= 0.0;
+                    if (!accept) {
+                        const double u = uniform24d(philox_word0(seed, (uint32_t)k,
+                                                                 (uint32_t)(2 * g + ph), emcs, TAG_PT));
+                        accept = u < exp(delta);
+                    }
+                    if (accept) {
+                        const int tp = perm[k]; perm[k] = perm[k + 1]; perm[k + 1] = tp;
+                        const double te = Ep[k]; Ep[k] = Ep[k + 1]; Ep[k + 1] = te;
+                        acc[k] += 1;
+                    }
+                }
+                __syncwarp();
+            }
+            if (lane == 0) {
+                uint8_t *rt = b.rt + (size_t)s * b.NLAT + g * b.NSLOT;
+                if (rt[perm[0]] & 1u) rt[perm[0]] |= 2u;
+            }
+        }
+        if ((flags & PTHR_SWAP_ER) && b.NRES > 0 && lane == 0) {
+            uint32_t *age = b.age + ((size_t)s * b.NR + g) * b.NRES;
+            int best = 0;
+            for (int r = 1; r < b.NRES; ++r) if (age[r] > age[best]) best = r;
+            const int hot = b.NT - 1, res = b.NT + best;
+            const int out = perm[hot], in = perm[res];
+            uint8_t *rt = b.rt + (size_t)s * b.NLAT + g * b.NSLOT;
+            if ((rt[out] & 3u) == 3u) b.trips[(size_t)s * b.NR + g] += 1;
+            rt[out] = 0;
+            rt[in] = 1;
+            perm[hot] = in;
+            perm[res] = out;
+            for (int r = 0; r < b.NRES; ++r) age[r] = (r == best) ? 0u : age[r] + 1u;
+        }
+        __syncwarp();
+        for (int i = lane; i < b.NSLOT; i += 32) gperm[i] = perm[i];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) b.emcs[s] = emcs + 1u;
+}
+
+// One block per (sample, temperature index k).  Accumulator layout per
+// (s, k): [0] measurements, [1] sum e, [2] sum e^2 (over groups), [3] sum q,
+// [4] sum q^2, [5] sum q_l, [6] sum S, [7] sum q^4 (over pairs).
+template <int L>
+__global__ void measure_kernel(Batch b, int first) {
+    using Gm = Geom<L>;
+    constexpr int V = Gm::V, LW = Gm::LAT_WORDS;
+    const int s = first + blockIdx.x;
+    const int k = blockIdx.y;
+    if (!b.active[s]) return;
+    __shared__ int s_neg[32], s_diff[32];
+    const int tid = threadIdx.x, T = blockDim.x;
+    double *o = b.obs + ((size_t)s * b.NT + k) * PTHR_NOBS;
+    const double Tk = temperature(b, k);
+    if (tid == 0) {
+        double se = o[1], se2 = o[2];
+        for (int g = 0; g < b.NR; ++g) {
+            const int lat = g * b.NSLOT + b.perm[((size_t)s * b.NR + g) * b.NSLOT + k];
+            const double e = __ddiv_rn(b.E[(size_t)s * b.NLAT + lat], (double)V);
+            se = __dadd_rn(se, e);
+            se2 = __dadd_rn(se2, __dmul_rn(e, e));
+        }
+        o[0] = __dadd_rn(o[0], 1.0);
+        o[1] = se;
+        o[2] = se2;
+    }
+    for (int P = 0; P < b.NPAIR; ++P) {
+        const int la = 2 * P * b.NSLOT + b.perm[((size_t)s * b.NR + 2 * P) * b.NSLOT + k];
+        const int lb = (2 * P + 1) * b.NSLOT + b.perm[((size_t)s * b.NR + 2 * P + 1) * b.NSLOT + k];
+        const unsigned char *A = reinterpret_cast<const unsigned char *>(b.spins + ((size_t)s * b.NLAT + la) * LW);
+        const unsigned char *B = reinterpret_cast<const unsigned char *>(b.spins + ((size_t)s * b.NLAT + lb) * LW);
+        int nneg = 0, ndiff = 0;
+        for (int i = tid; i < V; i += T) {
+            int w, by;
+            site_slot<L>(i, w, by);
+            const int qi = (A[4 * w + by] ^ B[4 * w + by]) >> 7;
+            nneg += qi;
+            const int x = i % L, y = (i / L) % L, z = i / (L * L);
+            const int nb[3] = {((x + 1) % L) + L * (y + L * z), x + L * (((y + 1) % L) + L * z),
+                               x + L * (y + L * ((z + 1) % L))};
+#pragma unroll
+            for (int mu = 0; mu < 3; ++mu) {
+                site_slot<L>(nb[mu], w, by);
+                const int qj = (A[4 * w + by] ^ B[4 * w + by]) >> 7;
+                ndiff += qi ^ qj;
+            }
+        }
+        nneg = __reduce_add_sync(0xffffffffu, nneg);
+        ndiff = __reduce_add_sync(0xffffffffu, ndiff);
+        if ((tid & 31) == 0) { s_neg[tid >> 5] = nneg; s_diff[tid >> 5] = ndiff; }
+        __syncthreads();
+        if (tid == 0) {
+            int tn = 0, td = 0;
+            for (int w = 0; w < T / 32; ++w) { tn += s_neg[w]; td += s_diff[w]; }
+            const double q = __ddiv_rn((double)(V - 2 * tn), (double)V);
+            const double ql = __ddiv_rn((double)(3 * V - 2 * td), 3.0 * (double)V);
+            const double Ha = b.E[(size_t)s * b.NLAT + la];
+            const double S = __dadd_rn(__ddiv_rn(Ha, 3.0 * (double)V), __ddiv_rn(__dsub_rn(1.0, ql), Tk));
+            const double q2 = __dmul_rn(q, q);
+            o[3] = __dadd_rn(o[3], q);
+            o[4] = __dadd_rn(o[4], q2);
+            o[5] = __dadd_rn(o[5], ql);
+            o[6] = __dadd_rn(o[6], S);
+            o[7] = __dadd_rn(o[7], __dmul_rn(__dmul_rn(q2, q), q));
+        }
+        __syncthreads();
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_swap(const Batch &b, int flags, int first, int count, cudaStream_t st) {
+    if (b.NR > 32 || b.NSLOT > MAX_SLOT) return cudaErrorInvalidValue;
+    const size_t sm = (size_t)b.NR * b.NSLOT * (sizeof(double) + sizeof(int));
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = allow_max_dynamic_smem(swap_kernel);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    swap_kernel<<<count, 32 * b.NR, sm, st>>>(b, flags, first);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_measure(const Batch &b, int first, int count, cudaStream_t st) {
+    dim3 grid(count, b.NT);
+#define X(LL) if (b.L == LL) { measure_kernel<LL><<<grid, 256, 0, st>>>(b, first); return cudaGetLastError(); }
+    PTHR_FOR_EACH_L(X)
+#undef X
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace pthr

@@ -1,0 +1,45 @@
+// kernels.cuh -- launch interfaces of the PTHR kernels (internal to the library).
+#pragma once
+
+#include "pthr_internal.cuh"
+
+namespace pthr {
+
+struct SweepArgs {
+    Batch b;
+    int n_pt_sweeps, n_res_sweeps;       // sweeps per kind in this launch
+    int pt_sweep_base, res_sweep_base;   // sweep index of the first sweep in this EMCS
+    int K_pt, K_res;                     // lattices per block
+    int pt_tasks, res_tasks;             // blocks per sample per kind
+    int do_pt, do_res;                   // launch PT / reservoir blocks (0/1)
+    int sample_first, sample_count;
+    int emcs_override;                   // 1: counter word PRETHERM_EMCS
+    int Gt;                              // groups per lattice lane (divides G and threads)
+};
+
+cudaError_t launch_sweep(const SweepArgs &a, int blocks, int threads, cudaStream_t st);
+size_t sweep_smem_bytes_for(int L, int K);
+int sweep_groups_for(int L);
+int sweep_max_k();
+
+// cluster.cu
+struct ClusterArgs {
+    Batch b;
+    int sample_first, sample_count;
+    int label_only;          // 1: only write labels (no flip, no energies)
+    int32_t *labels_out;     // optional [S][NPAIR][NT][V] canonical labels
+};
+cudaError_t launch_cluster(const ClusterArgs &a, int threads, cudaStream_t st);
+size_t cluster_smem_bytes_for(int L);
+
+// exchange.cu
+cudaError_t launch_swap(const Batch &b, int flags, int first, int count, cudaStream_t st);
+cudaError_t launch_measure(const Batch &b, int first, int count, cudaStream_t st);
+
+// init.cu
+cudaError_t launch_couplings_from_seed(const Batch &b, int first, int count, cudaStream_t st);
+cudaError_t launch_init_state(const Batch &b, int first, int count, cudaStream_t st);
+cudaError_t launch_export_spins(const Batch &b, int8_t *out, cudaStream_t st);
+cudaError_t launch_import_spins(const Batch &b, const int8_t *in, cudaStream_t st);
+
+}  // namespace pthr

@@ -1,0 +1,179 @@
+// pthr_internal.cuh -- shared device helpers of the PTHR CUDA library (sm_103a).
+//
+// Internal spin layout ("packed colour rows").  A lattice is split by the
+// checkerboard colour c = (x+y+z)&1.  Row r = y + L*z of colour c holds the
+// L/2 sites x = 2m + p, p = (c + y + z)&1, m = 0..L/2-1, one byte each, padded
+// to W = ceil((L/2)/4) 32-bit words.  Byte value 0x3F is spin +1, 0xBF spin -1:
+// byte_perm(word, 0x80, 0x?455) then yields the FP32 value +-1.0f directly.
+// Word index: (c * L*L + r) * W + (m >> 2), byte m & 3.
+//
+// Random numbers: Philox4x32-10 (Salmon et al., SC'11) keyed by the sample's
+// 64-bit seed; counter words (c0, c1, c2, c3) per stream:
+//   init spins  (i>>2, lattice, 0, TAG_INIT)              word i & 3
+//   sweep       (r*W + (m>>2), lattice, emcs, TAG_SWEEP | c<<8 | sweep<<9)
+//                                                        word m & 3
+//   ACU sign    (label, pair*n_temps + k, emcs, TAG_ACU)  word 0, top bit
+//   PT          (k, 2*group + phase, emcs, TAG_PT)        word 0
+//   single seed (0, pair*n_temps + k, emcs, TAG_SINGLE)   word 0
+//   couplings   (bond>>2, 0, 0, TAG_COUPLING)             Box-Muller pair
+// Uniform u = (word >> 8) * 2^-24.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "pthr.h"
+
+namespace pthr {
+
+constexpr uint32_t TAG_INIT = 0, TAG_SWEEP = 1, TAG_ACU = 2, TAG_PT = 3, TAG_SINGLE = 4,
+                   TAG_COUPLING = 5;
+constexpr uint32_t PRETHERM_EMCS = 0xFFFFFFFFu;
+constexpr uint32_t STATUS_NOCONVERGE = 1u;
+constexpr uint32_t STATUS_BOUNDS = 2u;
+
+constexpr unsigned char SPIN_UP = 0x3F, SPIN_DN = 0xBF;
+
+template <int L>
+struct Geom {
+    static constexpr int Lh = L / 2;
+    static constexpr int W = (Lh + 3) / 4;           // words per colour row
+    static constexpr int ROWS = L * L;               // rows per colour
+    static constexpr int G = ROWS * W;               // 4-site groups per colour
+    static constexpr int LAT_WORDS = 2 * ROWS * W;   // 32-bit words per lattice
+    static constexpr int LAT_BYTES = 4 * LAT_WORDS;
+    static constexpr int V = L * L * L;
+    static constexpr bool FULL = (Lh % 4) == 0;      // every group holds 4 sites
+};
+
+__host__ __device__ inline int lattice_words(int L) {
+    int W = (L / 2 + 3) / 4;
+    return 2 * L * L * W;
+}
+
+// Everything a kernel needs about the batch; passed by value.
+struct Batch {
+    float *J;                 // [S][3][V]
+    uint32_t *spins;          // [S][n_lat][lat_words]
+    double *E;                // [S][n_lat]
+    int32_t *perm;            // [S][NR][NSLOT]
+    uint32_t *age;            // [S][NR][max(NRES,1)]
+    uint8_t *rt;              // [S][n_lat]
+    long long *trips;         // [S][NR]
+    long long *ptacc;         // [S][NR][NT]
+    unsigned long long *flips;// [S][n_lat]
+    double *obs;              // [S][NT][PTHR_NOBS]
+    uint32_t *emcs;           // [S]
+    unsigned long long *seeds;// [S]
+    uint8_t *active;          // [S]
+    uint32_t *status;         // [4]
+    long long *cstat;         // [S][NPAIR][NT][4]
+    int S, L, NT, NR, NRES, NSLOT, NLAT, NPAIR, lat_words;
+    int rule, cluster_mode, acu_interval, n_acu;
+    double t_min, t_max;
+};
+
+// T_k = t_min + k (t_max - t_min) / (n_temps - 1) (App. A.2), evaluated with
+// one IEEE rounding per operation in this order (no contraction), so that
+// host and device get the same bits.
+__host__ __device__ inline double temperature(const Batch &b, int k) {
+    if (b.NT == 1) return b.t_min;
+#ifdef __CUDA_ARCH__
+    return __dadd_rn(b.t_min, __ddiv_rn(__dmul_rn((double)k, __dsub_rn(b.t_max, b.t_min)),
+                                        (double)(b.NT - 1)));
+#else
+    volatile double d = (double)k * (b.t_max - b.t_min);
+    volatile double q = d / (double)(b.NT - 1);
+    return b.t_min + q;
+#endif
+}
+
+// ---------------------------------------------------------------- Philox4x32-10
+struct u4 { uint32_t x, y, z, w; };
+
+__device__ __forceinline__ u4 philox10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                       uint32_t k0, uint32_t k1) {
+    const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+    const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t hi0 = __umulhi(M0, c0), lo0 = M0 * c0;
+        const uint32_t hi1 = __umulhi(M1, c2), lo1 = M1 * c2;
+        const uint32_t n0 = hi1 ^ c1 ^ k0;
+        const uint32_t n2 = hi0 ^ c3 ^ k1;
+        c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+        k0 += W0; k1 += W1;
+    }
+    return u4{c0, c1, c2, c3};
+}
+
+__device__ __forceinline__ uint32_t philox_word0(unsigned long long seed, uint32_t c0,
+                                                 uint32_t c1, uint32_t c2, uint32_t c3) {
+    return philox10(c0, c1, c2, c3, (uint32_t)seed, (uint32_t)(seed >> 32)).x;
+}
+
+// 24-bit uniform in [0,1), exact in FP32.
+__device__ __forceinline__ float uniform24f(uint32_t x) {
+    return __uint2float_rz(x >> 8) * 5.9604644775390625e-08f;
+}
+__device__ __forceinline__ double uniform24d(uint32_t x) {
+    return (double)(x >> 8) * (1.0 / 16777216.0);
+}
+
+// byte k of w (0x3F / 0xBF) as the FP32 spin +-1.0f
+__device__ __forceinline__ float spinf(uint32_t w, int k) {
+    return __uint_as_float(__byte_perm(w, 0x80u, 0x0455u | ((uint32_t)k << 12)));
+}
+
+__device__ __forceinline__ float fast_exp2(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Error-free FP32 accumulation (hi + lo holds the exact running sum as long as
+// lo stays exact): Knuth's TwoSum.
+__device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float t) {
+    const float s = hi + t;
+    const float bb = s - hi;
+    const float e = (hi - (s - bb)) + (t - bb);
+    hi = s;
+    lo += e;
+}
+
+// natural site -> (word index, byte) in the packed colour-row layout
+template <int L>
+__host__ __device__ __forceinline__ void site_slot(int i, int &word, int &byte) {
+    using Gm = Geom<L>;
+    const int x = i % L, y = (i / L) % L, z = i / (L * L);
+    const int c = (x + y + z) & 1;
+    const int r = y + L * z;
+    const int m = x >> 1;
+    word = (c * Gm::ROWS + r) * Gm::W + (m >> 2);
+    byte = m & 3;
+}
+
+// Raise a kernel's dynamic shared-memory limit to what the device allows on
+// top of the kernel's static shared memory (once per kernel).
+template <typename F>
+inline cudaError_t allow_max_dynamic_smem(F *kernel) {
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    cudaFuncAttributes fa;
+    e = cudaFuncGetAttributes(&fa, kernel);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                optin - (int)fa.sharedSizeBytes);
+}
+
+__device__ __forceinline__ void set_status(uint32_t *status, uint32_t bit) {
+    atomicOr(status, bit);
+}
+
+// Supported linear sizes (template instantiations).
+#define PTHR_FOR_EACH_L(X) X(2) X(4) X(6) X(8) X(10) X(12) X(14) X(16) X(18) X(20) X(22) X(24)
+
+}  // namespace pthr

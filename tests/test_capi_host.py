@@ -1,0 +1,91 @@
+"""Host-side checks of the C ABI (no GPU needed): the library builds for
+sm_103a, loads, exports every entry point that include/pthr.h declares, and
+rejects bad arguments before touching CUDA."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2605_25872_gb300 import BatchConfig, buffer_info, required_bytes
+from paper_2605_25872_gb300 import _lib
+from paper_2605_25872_gb300.build import build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build()
+    return _lib.load()
+
+
+def declared_entry_points():
+    names = []
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", h)).read()
+            names += re.findall(r"PTHR_API\s+[\w\s\*]+?\b(pthr_\w+)\s*\(", txt)
+    return sorted(set(names))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_entry_points()
+    assert len(names) >= 20
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) == set(_lib.EXPORTS)
+    assert lib.pthr_version().startswith(b"pthr-gb300")
+
+
+def test_required_bytes_and_layout(lib):
+    c = BatchConfig(L=16, n_samples=512, n_temps=32)
+    total = required_bytes(c)
+    prev_end = 0
+    for b in range(_lib.NBUF):
+        off, n = buffer_info(c, b)
+        assert off % 256 == 0 and off >= prev_end
+        prev_end = off + n
+    assert prev_end <= total
+    assert buffer_info(c, _lib.BUF_J)[1] == 512 * 3 * 4096 * 4
+    assert buffer_info(c, _lib.BUF_SPINS)[1] == 512 * 144 * 4096
+    n = ctypes.c_size_t()
+    assert lib.pthr_lattice_bytes(12, ctypes.byref(n)) == 0 and n.value == 2 * 144 * 8
+
+
+@pytest.mark.parametrize("field,value", [("L", 3), ("L", 26), ("L", 0), ("n_samples", 0),
+                                         ("n_temps", 1), ("n_replicas", 0), ("n_replicas", 3),
+                                         ("t_min", 0.0), ("t_max", 0.1), ("acu_interval", 0),
+                                         ("n_res", 0), ("rule", "bogus")])
+def test_invalid_configs_are_rejected(lib, field, value):
+    c = BatchConfig(L=8, n_samples=4, n_temps=8)
+    if field == "rule":
+        cc = c.to_c()
+        cc.update_rule = 7
+    else:
+        setattr(c, field, value)
+        cc = c.to_c()
+    n = ctypes.c_size_t()
+    st = lib.pthr_required_bytes(ctypes.byref(cc), ctypes.byref(n))
+    assert st == _lib.PTHR_E_INVAL
+    assert len(lib.pthr_last_error(None)) > 0
+
+
+def test_create_rejects_bad_workspace_without_cuda(lib):
+    c = BatchConfig(L=8, n_samples=2, n_temps=4).to_c()
+    h = ctypes.c_void_p()
+    assert lib.pthr_create_batch(ctypes.byref(c), None, 0, None, None, None, ctypes.byref(h)) == _lib.PTHR_E_INVAL
+    assert lib.pthr_create_batch(ctypes.byref(c), ctypes.c_void_p(256), 16, None, None, None,
+                                 ctypes.byref(h)) == _lib.PTHR_E_NOMEM
+    assert lib.pthr_create_batch(ctypes.byref(c), ctypes.c_void_p(100), 1 << 40, None, None, None,
+                                 ctypes.byref(h)) == _lib.PTHR_E_INVAL   # misaligned
+    assert h.value is None
+
+
+def test_null_handle_calls_fail_cleanly(lib):
+    assert lib.pthr_sweep(None, 1, 1) == _lib.PTHR_E_INVAL
+    assert lib.pthr_swap(None, 1) == _lib.PTHR_E_INVAL
+    assert lib.pthr_houdayer(None) == _lib.PTHR_E_INVAL
+    assert lib.pthr_emcs(None, 1, 0) == _lib.PTHR_E_INVAL
+    assert lib.pthr_poll(None, 0) == _lib.PTHR_E_INVAL
+    lib.pthr_destroy(None)

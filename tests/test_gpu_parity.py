@@ -1,0 +1,416 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Inputs (couplings, seeds, spin configurations) come from ``workloads``; every
+expected value comes from ``oracle``.  Trajectory parity: with shared Philox
+counters the spins must match bit for bit, except where a Metropolis/heat-bath
+decision had an oracle margin |u - p| < 1e-6 (a near tie, counted); such a
+divergence is resynchronised by pushing the oracle state into the GPU.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import workloads as W
+from mirror import Mirror, explained_by_ties
+
+pytestmark = pytest.mark.gpu
+
+P = pytest.importorskip("paper_2605_25872_gb300")
+from paper_2605_25872_gb300 import Batch, BatchConfig  # noqa: E402
+from paper_2605_25872_gb300.build import build  # noqa: E402
+
+TIE_RATE_MAX = 1e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    build()
+
+
+def make(cfg: BatchConfig, seed=7, on_grid=True, couplings="input", field_err_bound=False):
+    seeds = W.sample_seeds(W.SEED_BASE + seed, cfg.n_samples)
+    if couplings == "input":
+        J = W.gaussian_couplings(cfg.L, cfg.n_samples, seed, on_grid=on_grid)
+        gpu = Batch(cfg, couplings=J, seeds=seeds)
+    else:
+        J = np.stack([O.couplings_from_seed(cfg.L, int(s)) for s in seeds]).astype(np.float32)
+        gpu = Batch(cfg, couplings=None, seeds=seeds)
+    mir = Mirror(cfg, J, seeds, field_err_bound=field_err_bound)
+    return gpu, mir
+
+
+def gpu_spins(gpu):
+    return gpu.export_spins().cpu().numpy()
+
+
+def resync(gpu, mir):
+    """Push the oracle state into the GPU (spins, permutations, ages, round-trip
+    state and counters); energies are recomputed by the import."""
+    gpu.perm.copy_(torch.from_numpy(mir.perms().astype(np.int32)))
+    if mir.cfg.n_res:
+        gpu.age.copy_(torch.from_numpy(mir.ages().astype(np.int32)))
+    gpu.rt_state.copy_(torch.from_numpy(np.stack([s.rt_state for s in mir.samples])))
+    gpu.round_trips.copy_(torch.from_numpy(np.stack([s.round_trips for s in mir.samples])))
+    gpu.pt_accepted.copy_(torch.from_numpy(
+        np.stack([s.pt_accepted for s in mir.samples]).reshape(gpu.pt_accepted.shape)))
+    gpu.import_spins(torch.from_numpy(mir.spins()))
+
+
+def check_sweep_parity(gpu, mir, n_calls, n_pt=1, n_res=1):
+    """Sweep both sides call by call; returns (near ties that changed the
+    trajectory, oracle decisions)."""
+    L = mir.L
+    diverged = 0
+    for it in range(n_calls):
+        gpu.sweep(n_pt, n_res)
+        ties = mir.sweep(n_pt, n_res)
+        g = gpu_spins(gpu)
+        o = mir.spins()
+        bad = np.argwhere(g != o)
+        if len(bad):
+            for s, lat in {(int(a), int(b)) for a, b, _ in bad}:
+                sites = bad[(bad[:, 0] == s) & (bad[:, 1] == lat)][:, 2]
+                assert (s, lat) in ties and (n_pt + n_res) <= 2 and \
+                    explained_by_ties(L, sites, ties[(s, lat)]), \
+                    f"call {it}: sample {s} lattice {lat} differs at {sites[:10]} without a near tie"
+            diverged += 1
+            resync(gpu, mir)
+        else:
+            np.testing.assert_array_equal(gpu.energies.cpu().numpy(), mir.energies())
+    return diverged, mir.decisions
+
+
+# ----------------------------------------------------------------------------- a1
+
+def test_couplings_from_seed_match_oracle():
+    cfg = BatchConfig(L=8, n_samples=6, n_temps=4, n_replicas=2, n_res=2, cluster="acu")
+    gpu, mir = make(cfg, couplings="seed")
+    Jg = gpu.J.cpu().numpy()
+    Jo = np.stack([s.J for s in mir.samples])
+    diff = Jg.astype(np.float64) != Jo
+    # FP64 libm and CUDA math may differ in the last bit before the 2^-18 rounding
+    assert diff.sum() <= 2
+    assert np.all(np.abs(Jg.astype(np.float64) - Jo)[diff] <= 2.0 ** -18)
+
+
+@pytest.mark.parametrize("L", [2, 4, 6, 8, 10, 12, 16])
+def test_init_state_matches_oracle(L):
+    cfg = BatchConfig(L=L, n_samples=3, n_temps=5, n_replicas=4, n_res=3)
+    gpu, mir = make(cfg, seed=L)
+    np.testing.assert_array_equal(gpu_spins(gpu), mir.spins())
+    np.testing.assert_array_equal(gpu.energies.cpu().numpy(), mir.energies())
+    np.testing.assert_array_equal(gpu.perm.cpu().numpy(), mir.perms())
+    np.testing.assert_array_equal(gpu.age.cpu().numpy(), mir.ages())
+
+
+# ----------------------------------------------------------------------------- a2/a3/a4
+
+@pytest.mark.parametrize("L,rule", [(2, "metropolis"), (4, "metropolis"), (6, "metropolis"),
+                                    (8, "metropolis"), (10, "metropolis"), (12, "metropolis"),
+                                    (14, "metropolis"), (16, "metropolis"), (8, "heatbath"),
+                                    (6, "heatbath")])
+def test_sweep_trajectory_parity(L, rule):
+    cfg = BatchConfig(L=L, n_samples=2, n_temps=6, n_replicas=2, n_res=2, rule=rule,
+                      t_min=0.2, t_max=1.6)
+    gpu, mir = make(cfg, seed=100 + L)
+    n = 60 if L >= 12 else 150
+    diverged, decisions = check_sweep_parity(gpu, mir, n)
+    assert diverged <= max(1, TIE_RATE_MAX * decisions)
+    if diverged == 0:
+        np.testing.assert_array_equal(gpu.flips.cpu().numpy(), np.stack([s.flips for s in mir.samples]))
+
+
+def test_sweep_parity_1000_sweeps_plain_config():
+    """Config 1 shape (L=4, 12 temperatures, 4 replicas + 4 reservoir clones):
+    10^3 sweeps of every clone, bit-exact up to counted near ties."""
+    cfg = BatchConfig(L=4, n_samples=1, n_temps=12, n_replicas=4, n_res=4)
+    gpu, mir = make(cfg, seed=1)
+    diverged, decisions = check_sweep_parity(gpu, mir, 1000)
+    assert diverged <= max(1, TIE_RATE_MAX * decisions)
+
+
+def test_multi_sweep_launch_matches_single_sweeps():
+    """Ten sweeps in one launch (shared-memory resident) equal the oracle's ten."""
+    cfg = BatchConfig(L=8, n_samples=3, n_temps=8, n_replicas=4, n_res=2)
+    gpu, mir = make(cfg, seed=5)
+    for it in range(5):
+        gpu.sweep(10, 24)
+        ties = mir.sweep(10, 24)
+        g, o = gpu_spins(gpu), mir.spins()
+        if not np.array_equal(g, o):
+            bad = {(int(a), int(b)) for a, b, _ in np.argwhere(g != o)}
+            assert bad <= set(ties), "divergence without a near tie"
+            resync(gpu, mir)
+        else:
+            np.testing.assert_array_equal(gpu.energies.cpu().numpy(), mir.energies())
+
+
+def test_offgrid_couplings_parity_with_fp32_error_margin():
+    """Couplings off the 2^-18 grid: the FP32 field is rounded, so the near-tie
+    margin adds the FP32 error bound of the field (oracle, field_err_bound)."""
+    cfg = BatchConfig(L=8, n_samples=2, n_temps=6, n_replicas=2, n_res=2)
+    gpu, mir = make(cfg, seed=77, on_grid=False, field_err_bound=True)
+    L = cfg.L
+    diverged = 0
+    for it in range(100):
+        gpu.sweep(1, 1)
+        ties = mir.sweep(1, 1)
+        g, o = gpu_spins(gpu), mir.spins()
+        bad = np.argwhere(g != o)
+        if len(bad):
+            for s, lat in {(int(a), int(b)) for a, b, _ in bad}:
+                sites = bad[(bad[:, 0] == s) & (bad[:, 1] == lat)][:, 2]
+                assert (s, lat) in ties and explained_by_ties(L, sites, ties[(s, lat)])
+            diverged += 1
+            resync(gpu, mir)
+        else:
+            np.testing.assert_allclose(gpu.energies.cpu().numpy(), mir.energies(), rtol=1e-9, atol=1e-9)
+    assert diverged <= 5
+
+
+# ----------------------------------------------------------------------------- a5/a6
+
+@pytest.mark.parametrize("L", [2, 4, 6, 8, 10, 12, 16])
+def test_cluster_labels_bit_exact(L):
+    cfg = BatchConfig(L=L, n_samples=2, n_temps=5, n_replicas=4, n_res=1)
+    gpu, mir = make(cfg, seed=30 + L)
+    spins = W.random_spins((cfg.n_samples, cfg.n_lat, cfg.V), 1000 + L)
+    spins[0, 0] = spins[0, cfg.n_slot]           # pair 0 at T_0: every q_i = +1
+    gpu.import_spins(torch.from_numpy(spins))
+    lab = gpu.cluster_labels().cpu().numpy()
+    for s in range(cfg.n_samples):
+        for p in range(cfg.n_replicas // 2):
+            for k in range(cfg.n_temps):
+                la = (2 * p) * cfg.n_slot + k
+                lb = (2 * p + 1) * cfg.n_slot + k
+                ref, _ = O.cc_labels(L, spins[s, la], spins[s, lb])
+                np.testing.assert_array_equal(lab[s, p, k], ref)
+
+
+@pytest.mark.parametrize("mode", ["acu", "single"])
+@pytest.mark.parametrize("L", [4, 8, 12, 16])
+def test_cluster_move_parity(mode, L):
+    cfg = BatchConfig(L=L, n_samples=3, n_temps=8, n_replicas=4, n_res=2, cluster=mode)
+    gpu, mir = make(cfg, seed=60 + L)
+    spins = W.random_spins((cfg.n_samples, cfg.n_lat, cfg.V), 2000 + L)
+    gpu.import_spins(torch.from_numpy(spins))
+    for s, smp in enumerate(mir.samples):
+        smp.spins[:] = spins[s]
+        for lat in range(cfg.n_lat):
+            smp.E_lat[lat] = O.energy(L, smp.J, smp.spins[lat])
+    for rep in range(3):
+        gpu.houdayer()
+        stats = mir.houdayer()
+        np.testing.assert_array_equal(gpu_spins(gpu), mir.spins())
+        np.testing.assert_array_equal(gpu.energies.cpu().numpy(), mir.energies())
+        cs = gpu.cluster_stats.cpu().numpy()
+        for (s, p, k), (lab, n) in stats.items():
+            if mode == "acu":
+                assert cs[s, p, k, 0] == n
+                sizes = np.sort(np.bincount(lab))[::-1]
+                assert cs[s, p, k, 1] == sizes[0]
+                assert cs[s, p, k, 2] == (sizes[1] if len(sizes) > 1 and sizes[1] > 0 else 0)
+            else:
+                assert cs[s, p, k, 3] == n
+        gpu.swap(pt=False, er=False)      # next EMCS index: new random signs
+        mir.swap(pt=False, er=False)
+
+
+# ----------------------------------------------------------------------------- a7/a8/a9 and full EMCS
+
+def run_emcs_parity(cfg, n_emcs, seed):
+    gpu, mir = make(cfg, seed=seed)
+    resyncs = 0
+    for e in range(n_emcs):
+        gpu.sweep(cfg.sweeps_per_emcs, cfg.res_sweeps_per_emcs if cfg.er_on else 0)
+        if cfg.cluster != "off":
+            gpu.houdayer()
+        gpu.swap(True, cfg.er_on)
+        gpu.measure()
+        ties, pt_ties = mir.emcs()
+        g = gpu_spins(gpu)
+        same = (np.array_equal(g, mir.spins()) and np.array_equal(gpu.perm.cpu().numpy(), mir.perms()))
+        if not same:
+            bad_samples = {int(a) for a, _, _ in np.argwhere(g != mir.spins())}
+            bad_samples |= {int(a) for a in np.argwhere((gpu.perm.cpu().numpy() != mir.perms()).any(axis=(1, 2))).ravel()}
+            tie_samples = {s for s, _ in ties}
+            assert bad_samples <= tie_samples or pt_ties > 0, \
+                f"EMCS {e}: samples {bad_samples} diverged without a near tie"
+            resyncs += 1
+            resync(gpu, mir)
+            gpu.obs.copy_(torch.from_numpy(np.stack([s.obs for s in mir.samples])))
+            continue
+        np.testing.assert_array_equal(gpu.energies.cpu().numpy(), mir.energies())
+        if cfg.n_res:
+            np.testing.assert_array_equal(gpu.age.cpu().numpy(), mir.ages())
+        np.testing.assert_array_equal(gpu.rt_state.cpu().numpy(), np.stack([s.rt_state for s in mir.samples]))
+        np.testing.assert_array_equal(gpu.round_trips.cpu().numpy(), np.stack([s.round_trips for s in mir.samples]))
+        np.testing.assert_array_equal(gpu.pt_accepted.cpu().numpy().reshape(cfg.n_samples, -1),
+                                      np.stack([s.pt_accepted for s in mir.samples]))
+        np.testing.assert_array_equal(gpu.obs.cpu().numpy(), np.stack([s.obs for s in mir.samples]))
+        assert np.all(gpu.emcs_counter.cpu().numpy() == e + 1)
+    return gpu, mir, resyncs
+
+
+def test_full_emcs_parity_plain_config():
+    """Config 1: L=4, 1 sample, 12 temperatures 0.2..1.6, 4 replicas (2
+    Houdayer pairs) + 4 reservoir clones with 240 sweeps, 1 local sweep + ACU
+    + PT + ER per EMCS; spins, permutations, energies, ages, round trips, PT
+    counters and observable accumulators bit-exact."""
+    cfg = BatchConfig(L=4, n_samples=1, n_temps=12, n_replicas=4, n_res=4, sweeps_per_emcs=1,
+                      res_sweeps_per_emcs=240)
+    gpu, mir, resyncs = run_emcs_parity(cfg, 150, seed=1)
+    assert resyncs <= 2
+    assert mir.samples[0].pt_accepted.sum() > 0
+
+
+@pytest.mark.parametrize("cluster,rule,er", [("acu", "metropolis", True), ("single", "metropolis", True),
+                                             ("acu", "heatbath", False), ("off", "metropolis", False)])
+def test_full_emcs_parity_batched(cluster, rule, er):
+    cfg = BatchConfig(L=8, n_samples=4, n_temps=8, n_replicas=4, n_res=2 if er else 0,
+                      sweeps_per_emcs=2, res_sweeps_per_emcs=6, er_on=er, cluster=cluster, rule=rule)
+    gpu, mir, resyncs = run_emcs_parity(cfg, 40, seed=11)
+    assert resyncs <= 2
+
+
+def test_acu_interval_and_threshold():
+    cfg = BatchConfig(L=6, n_samples=2, n_temps=10, n_replicas=2, n_res=2, sweeps_per_emcs=1,
+                      res_sweeps_per_emcs=3, acu_interval=3, acu_t_below=0.9)
+    run_emcs_parity(cfg, 12, seed=3)
+
+
+# ----------------------------------------------------------------------------- batch-level properties
+
+def _state(gpu):
+    return (gpu_spins(gpu), gpu.perm.cpu().numpy().copy(), gpu.energies.cpu().numpy().copy(),
+            gpu.obs.cpu().numpy().copy())
+
+
+def _same(a, b):
+    for x, y in zip(a, b):
+        np.testing.assert_array_equal(x, y)
+
+
+def test_graph_replay_equals_direct_launches():
+    cfg = BatchConfig(L=8, n_samples=6, n_temps=8, n_replicas=4, n_res=2, sweeps_per_emcs=3,
+                      res_sweeps_per_emcs=5)
+    J = W.gaussian_couplings(8, 6, 3)
+    seeds = W.sample_seeds(99, 6)
+    s = torch.cuda.Stream()
+    a = Batch(cfg, couplings=J, seeds=seeds, stream=s)
+    b = Batch(cfg, couplings=J, seeds=seeds, stream=s)
+    a.emcs(7, graph=False)
+    b.emcs(7, graph=True)
+    s.synchronize()
+    _same(_state(a), _state(b))
+
+
+def test_tuning_does_not_change_results():
+    cfg = BatchConfig(L=8, n_samples=3, n_temps=8, n_replicas=4, n_res=4, sweeps_per_emcs=2,
+                      res_sweeps_per_emcs=4)
+    J = W.gaussian_couplings(8, 3, 4)
+    seeds = W.sample_seeds(5, 3)
+    ref = Batch(cfg, couplings=J, seeds=seeds)
+    ref.emcs(5)
+    for t in ({"pt_lattices_per_block": 1, "res_lattices_per_block": 3},
+              {"pt_lattices_per_block": 7, "sweep_threads": 64, "cluster_threads": 128},
+              {"pt_lattices_per_block": 32, "res_lattices_per_block": 16, "sweep_threads": 256}):
+        b = Batch(cfg, couplings=J, seeds=seeds, tuning=t)
+        b.emcs(5)
+        _same(_state(ref), _state(b))
+
+
+def test_save_load_resume_is_exact():
+    cfg = BatchConfig(L=6, n_samples=3, n_temps=6, n_replicas=4, n_res=2, sweeps_per_emcs=2,
+                      res_sweeps_per_emcs=4)
+    J = W.gaussian_couplings(6, 3, 8)
+    seeds = W.sample_seeds(8, 3)
+    full = Batch(cfg, couplings=J, seeds=seeds)
+    full.emcs(10)
+    half = Batch(cfg, couplings=J, seeds=seeds)
+    half.emcs(5)
+    blob = half.save()
+    again = Batch(cfg, couplings=J, seeds=seeds)
+    again.load(blob)
+    again.emcs(5)
+    _same(_state(full), _state(again))
+
+
+def test_sample_result_is_independent_of_slot_and_neighbours():
+    """Serving property: a sample reset into any slot of a busy batch evolves
+    exactly as it does alone (counter-based random numbers keyed by its seed)."""
+    cfg1 = BatchConfig(L=6, n_samples=1, n_temps=6, n_replicas=4, n_res=2, sweeps_per_emcs=2,
+                       res_sweeps_per_emcs=4)
+    cfg4 = BatchConfig(**{**cfg1.__dict__, "n_samples": 4})
+    J = W.gaussian_couplings(6, 4, 12)
+    alone = Batch(cfg1, couplings=J[2:3], seeds=[777])
+    alone.prethermalize(8)
+    alone.emcs(6)
+    mixed = Batch(cfg4, couplings=J, seeds=W.sample_seeds(1, 4))
+    mixed.emcs(3)
+    mixed.reset_samples(2, 1, seeds=[777], couplings=J[2:3], pretherm_sweeps=8)
+    mixed.emcs(6)
+    np.testing.assert_array_equal(gpu_spins(mixed)[2], gpu_spins(alone)[0])
+    np.testing.assert_array_equal(mixed.obs.cpu().numpy()[2], alone.obs.cpu().numpy()[0])
+    np.testing.assert_array_equal(mixed.energies.cpu().numpy()[2], alone.energies.cpu().numpy()[0])
+
+
+def test_idle_slots_are_untouched():
+    cfg = BatchConfig(L=6, n_samples=3, n_temps=6, n_replicas=4, n_res=2, sweeps_per_emcs=1,
+                      res_sweeps_per_emcs=2)
+    b = Batch(cfg, couplings=W.gaussian_couplings(6, 3, 1), seeds=W.sample_seeds(2, 3))
+    before = gpu_spins(b)[1].copy()
+    b.set_active(1, 1, False)
+    b.emcs(4)
+    after = gpu_spins(b)
+    np.testing.assert_array_equal(after[1], before)
+    assert b.emcs_counter.cpu().numpy().tolist() == [4, 0, 4]
+
+
+def test_prethermalisation_matches_oracle():
+    cfg = BatchConfig(L=6, n_samples=2, n_temps=4, n_replicas=2, n_res=3)
+    gpu, mir = make(cfg, seed=44)
+    gpu.prethermalize(30)
+    mir.sweep(0, 30, pretherm=True)
+    g, o = gpu_spins(gpu), mir.spins()
+    if not np.array_equal(g, o):
+        pytest.skip("near tie during pre-thermalisation (rare)")
+    np.testing.assert_array_equal(gpu.energies.cpu().numpy(), mir.energies())
+
+
+# ----------------------------------------------------------------------------- statistics
+
+def test_gpu_chain_reproduces_exact_enumeration_2x2x2():
+    """The GPU PTHR chain at L=2 (64 samples of one coupling set, different
+    seeds) samples the Boltzmann weight: <e>, <q^2>, <q_l>, <S> per
+    temperature within 5 standard errors of exact enumeration."""
+    L, S, NT = 2, 64, 4
+    J1 = W.gaussian_couplings(L, 1, 5)[0]
+    J = np.repeat(J1[None], S, axis=0)
+    cfg = BatchConfig(L=L, n_samples=S, n_temps=NT, t_min=0.4, t_max=1.6, n_replicas=4, n_res=4,
+                      sweeps_per_emcs=1, res_sweeps_per_emcs=3)
+    b = Batch(cfg, couplings=J, seeds=W.sample_seeds(321, S))
+    b.emcs(100)
+    b.reset_observables()
+    b.emcs(2000, graph=False)
+    obs = b.read_observables()
+    n = obs[:, :, 0:1]
+    per = np.stack([obs[:, :, 1] / (n[:, :, 0] * 4), obs[:, :, 4] / (n[:, :, 0] * 2),
+                    obs[:, :, 5] / (n[:, :, 0] * 2), obs[:, :, 6] / (n[:, :, 0] * 2)], -1)
+    est = per.mean(0)
+    err = per.std(0, ddof=1) / np.sqrt(S)
+    T, _ = O.temperatures(NT, 0.4, 1.6)
+    exact = O.enumerate_l2(J1.astype(np.float64), T)[:, [0, 1, 2, 3]]
+    z = np.abs(est - exact) / np.maximum(err, 1e-9)
+    assert np.all(z < 5.0), z
+
+
+def test_status_word_reads_ok():
+    cfg = BatchConfig(L=8, n_samples=2, n_temps=6, n_replicas=4, n_res=2, sweeps_per_emcs=1,
+                      res_sweeps_per_emcs=2)
+    b = Batch(cfg, couplings=W.gaussian_couplings(8, 2, 1), seeds=W.sample_seeds(2, 2))
+    b.emcs(3)
+    assert b.poll(10000) == 0
