@@ -17,7 +17,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libpthr.so")
-SOURCES = ["capi.cu", "sweep.cu", "cluster.cu", "exchange.cu", "init.cu"]
+SOURCES = ["capi.cu", "sweep.cu", "sweep_inst_metro_a.cu", "sweep_inst_metro_b.cu",
+           "sweep_inst_hb.cu", "cluster.cu", "exchange.cu", "init.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -131,15 +131,16 @@ Layout make_layout(const pthr_config *c) {
     return l;
 }
 
-// Kernel shapes.  Sweep: lattices per block K (PT / reservoir), groups per
-// lattice lane Gt (divides G, <= 512), threads = P * Gt.
-struct SweepShape { int K_pt, K_res, Gt, threads, pt_tasks, res_tasks; };
+// Kernel shapes.  Sweep: lattices per block K (PT / reservoir); Gt 4-site
+// groups per lattice lane (divides G, <= 512); P lattice lanes of KT
+// lattices each (KT one of the compiled variants); threads = P * Gt.
+struct SweepShape { int K_pt, K_res, Gt, P, KT, threads, pt_tasks, res_tasks; };
 
 int default_k(const pthr_config *c, int total_entries) {
     const size_t lb = (size_t)lattice_words(c->L) * 4;
     const size_t budget = 220 * 1024;
     long k = (long)((budget - 12 * lb) / lb);
-    if (c->L == 16) k = 16;             // two blocks per SM
+    if (c->L == 16) k = 16;
     if (k > sweep_max_k()) k = sweep_max_k();
     if (k < 1) k = 1;
     if (k > total_entries) k = total_entries;
@@ -162,12 +163,25 @@ SweepShape sweep_shape(const pthr_batch *b) {
             if (G % d == 0 && G / d <= 512) { Gt = G / d; break; }
     }
     sh.Gt = Gt;
-    const int Kmax = sh.K_pt > sh.K_res ? sh.K_pt : sh.K_res;
-    int P = 512 / Gt;
-    if (b->tuning.sweep_threads > 0) P = b->tuning.sweep_threads / Gt;
-    if (P < 1) P = 1;
-    if (P > Kmax) P = Kmax;
-    sh.threads = P * Gt;
+    int P0 = 512 / Gt;
+    if (b->tuning.sweep_threads > 0) P0 = b->tuning.sweep_threads / Gt;
+    if (P0 < 1) P0 = 1;
+    int opts[16];
+    const int nopt = sweep_kt_options(c->L, c->update_rule, opts);
+    int Kmax = sh.K_pt > sh.K_res ? sh.K_pt : sh.K_res;
+    if (P0 > Kmax) P0 = Kmax;
+    const int need = (Kmax + P0 - 1) / P0;
+    int KT = opts[nopt - 1];
+    for (int i = 0; i < nopt; ++i)
+        if (opts[i] >= need) { KT = opts[i]; break; }
+    if (P0 * KT < Kmax) {            // largest variant too small: fewer lattices per block
+        if (sh.K_pt > P0 * KT) sh.K_pt = P0 * KT;
+        if (sh.K_res > P0 * KT) sh.K_res = P0 * KT;
+        Kmax = sh.K_pt > sh.K_res ? sh.K_pt : sh.K_res;
+    }
+    sh.KT = KT;
+    sh.P = (Kmax + KT - 1) / KT;
+    sh.threads = sh.P * Gt;
     sh.pt_tasks = (npt + sh.K_pt - 1) / sh.K_pt;
     sh.res_tasks = (nres + sh.K_res - 1) / sh.K_res;
     return sh;
@@ -197,7 +211,7 @@ pthr_status do_sweep(pthr_batch *b, int n_pt, int n_res, int first, int count, i
     const size_t smem = sweep_smem_bytes_for(c->L, sh.K_pt > sh.K_res ? sh.K_pt : sh.K_res);
     if (smem > 220 * 1024)
         return fail(b, PTHR_E_INVAL, "sweep block needs %zu bytes of shared memory; lower the lattices per block", smem);
-    CUDA_TRY(b, launch_sweep(a, blocks, sh.threads, b->stream), "sweep launch");
+    CUDA_TRY(b, launch_sweep(a, blocks, sh.threads, sh.KT, b->stream), "sweep launch");
     return PTHR_OK;
 }
 
@@ -368,7 +382,7 @@ PTHR_API pthr_status pthr_set_tuning(pthr_batch *b, const pthr_tuning *t) {
     if (t) nt = *t;
     if (nt.pt_lattices_per_block < 0 || nt.pt_lattices_per_block > sweep_max_k() ||
         nt.res_lattices_per_block < 0 || nt.res_lattices_per_block > sweep_max_k() ||
-        nt.sweep_threads < 0 || nt.sweep_threads > 512 || nt.cluster_threads < 0 || nt.cluster_threads > 1024)
+        nt.sweep_threads < 0 || nt.sweep_threads > 512 || nt.cluster_threads < 0 || nt.cluster_threads > 512)
         return fail(b, PTHR_E_INVAL, "tuning out of range");
     pthr_tuning old = b->tuning;
     b->tuning = nt;

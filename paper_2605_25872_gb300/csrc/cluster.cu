@@ -56,7 +56,7 @@ __device__ __forceinline__ unsigned char spin_byte(const unsigned char *S, int i
 }
 
 template <int L>
-__global__ void __launch_bounds__(1024) cluster_kernel(ClusterArgs a) {
+__global__ void __launch_bounds__(512) cluster_kernel(ClusterArgs a) {
     using Gm = Geom<L>;
     constexpr int V = Gm::V, LW = Gm::LAT_WORDS;
     extern __shared__ __align__(16) unsigned char smem[];

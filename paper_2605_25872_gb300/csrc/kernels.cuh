@@ -17,10 +17,11 @@ struct SweepArgs {
     int Gt;                              // groups per lattice lane (divides G and threads)
 };
 
-cudaError_t launch_sweep(const SweepArgs &a, int blocks, int threads, cudaStream_t st);
+cudaError_t launch_sweep(const SweepArgs &a, int blocks, int threads, int KT, cudaStream_t st);
 size_t sweep_smem_bytes_for(int L, int K);
 int sweep_groups_for(int L);
 int sweep_max_k();
+int sweep_kt_options(int L, int rule, int *out);   // compiled lattices-per-thread values
 
 // cluster.cu
 struct ClusterArgs {

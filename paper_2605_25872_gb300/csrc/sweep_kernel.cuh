@@ -1,0 +1,357 @@
+// sweep_kernel.cuh -- step (i) of the EMCS (Sec. 3; App. A.1): checkerboard
+// Metropolis / heat-bath sweeps of many lattices of one sample per block,
+// with the couplings and the spins held in shared memory, followed by every
+// swept lattice's FP64 energy (Eq. (1)).
+//
+// Block = (sample, up to K lattices of one kind: PT clones or reservoir
+// clones).  The block loads the sample's couplings (FP32) into shared memory
+// in the packed colour-row layout and its lattices' spins (one byte each),
+// runs all its sweeps without touching global memory, then writes the spins
+// back.  Thread = (lattice lane p, 4-site group g): it owns one 4-site group
+// (4 consecutive same-colour sites of a row = one Philox call) of KT
+// consecutive lattices, so the group's 24 couplings stay in registers while
+// it walks its lattices, and the lattice loop unrolls with immediate
+// shared-memory offsets.
+//
+// Metropolis (App. A.1): with t_i = sum_j J_ij s_i s_j (the six products
+// s_i s_j come from one 3-input XOR of the site word with each neighbour
+// word), Delta E = 2 t_i and the move is accepted iff u < 2^(tb t_i) with
+// tb = -2 log2(e) / T, i.e. iff the FP32 difference u - p is negative; the
+// four sign bits of one group become the byte flip mask with three byte
+// permutes.  Heat bath: s_i = +1 iff u < 1 / (1 + 2^(tb h_i)).
+#pragma once
+
+#include "kernels.cuh"
+
+namespace pthr {
+namespace sweep_detail {
+
+constexpr int MAXK = 64;   // lattices per block
+
+struct GroupGeo {
+    int own, xa, yp, ym, zp, zm;   // word offsets in a lattice
+    int wA, wB;                    // words of the shifted x neighbour
+    uint32_t selx;                 // byte_perm selector of the shifted x word
+    int par;                       // x parity of this row/colour
+};
+
+// Geometry of 4-site group g of colour c (see pthr_internal.cuh for layout).
+template <int L>
+__device__ __forceinline__ GroupGeo group_geo(int g, int c) {
+    using Gm = Geom<L>;
+    constexpr int W = Gm::W, ROWS = Gm::ROWS, Lh = Gm::Lh;
+    GroupGeo q;
+    const int r = g / W, j = g - (g / W) * W;
+    const int y = r % L, z = r / L;
+    const int cc = c ^ 1;
+    q.par = (c + y + z) & 1;
+    const int ryp = ((y + 1) % L) + L * z, rym = ((y + L - 1) % L) + L * z;
+    const int rzp = y + L * ((z + 1) % L), rzm = y + L * ((z + L - 1) % L);
+    q.own = (c * ROWS + r) * W + j;
+    const int rowcc = (cc * ROWS + r) * W;
+    q.xa = rowcc + j;
+    q.yp = (cc * ROWS + ryp) * W + j;
+    q.ym = (cc * ROWS + rym) * W + j;
+    q.zp = (cc * ROWS + rzp) * W + j;
+    q.zm = (cc * ROWS + rzm) * W + j;
+    // Shifted x neighbour: m' = m - 1 (par 0, the -x neighbour) or m + 1
+    // (par 1, the +x neighbour), cyclic in [0, Lh).  At most two words.
+    const int d = q.par ? 1 : Lh - 1;
+    int wa = -1, wb = -1;
+    uint32_t sel = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        int m = 4 * j + k;
+        if (m >= Lh) m = Lh - 1;              // padding byte: any valid source
+        const int mp = (m + d) % Lh;
+        const int w = mp >> 2, by = mp & 3;
+        int src;
+        if (wa < 0 || wa == w) { wa = w; src = by; }
+        else { wb = w; src = 4 + by; }
+        sel |= (uint32_t)src << (4 * k);
+    }
+    if (wb < 0) wb = wa;
+    q.wA = rowcc + wa;
+    q.wB = rowcc + wb;
+    q.selx = sel;
+    return q;
+}
+
+// Philox4x32-10 with the ten round keys precomputed (the key is the sample
+// seed, the same for the whole block).
+__device__ __forceinline__ u4 philox10_rk(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                          const uint32_t (&rk0)[10], const uint32_t (&rk1)[10]) {
+    const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t hi0 = __umulhi(M0, c0), lo0 = M0 * c0;
+        const uint32_t hi1 = __umulhi(M1, c2), lo1 = M1 * c2;
+        const uint32_t n0 = hi1 ^ c1 ^ rk0[r];
+        const uint32_t n2 = hi0 ^ c3 ^ rk1[r];
+        c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+    }
+    return u4{c0, c1, c2, c3};
+}
+
+template <int L, int RULE, int KT>
+__global__ void __launch_bounds__(512) sweep_kernel(SweepArgs a) {
+    using Gm = Geom<L>;
+    constexpr int W = Gm::W, ROWS = Gm::ROWS, Lh = Gm::Lh, G = Gm::G;
+    constexpr int LW = Gm::LAT_WORDS, LB = Gm::LAT_BYTES;
+    extern __shared__ __align__(16) unsigned char smem[];
+    float *Js = reinterpret_cast<float *>(smem);                       // [3][LB]
+    uint32_t *Ss = reinterpret_cast<uint32_t *>(smem + 12 * LB);       // [K][LW]
+    __shared__ int s_lat[MAXK];
+    __shared__ float s_tb[MAXK];
+    __shared__ unsigned int s_flips[MAXK];
+    __shared__ double s_E[MAXK];
+
+    const Batch &b = a.b;
+    // ---- decode the task
+    int t = blockIdx.x;
+    const int nres_tasks = a.do_res ? a.res_tasks : 0;
+    const int nall_res = a.sample_count * nres_tasks;
+    int s, kind, chunk;
+    if (t < nall_res) { s = a.sample_first + t / nres_tasks; chunk = t % nres_tasks; kind = 1; }
+    else {
+        t -= nall_res;
+        if (!a.do_pt) return;
+        s = a.sample_first + t / a.pt_tasks; chunk = t % a.pt_tasks; kind = 0;
+    }
+    if (!b.active[s]) return;
+    const int per = kind ? b.NRES : b.NT;
+    const int total = b.NR * per;
+    const int Kmax = kind ? a.K_res : a.K_pt;
+    const int e0 = chunk * Kmax;
+    const int K = min(Kmax, total - e0);
+    if (K <= 0) return;
+    const int nsw = kind ? a.n_res_sweeps : a.n_pt_sweeps;
+    const int sweep_base = kind ? a.res_sweep_base : a.pt_sweep_base;
+    const uint32_t emcs = a.emcs_override ? PRETHERM_EMCS : b.emcs[s];
+    const unsigned long long seed = b.seeds[s];
+    const int tid = threadIdx.x, T = blockDim.x;
+
+    uint32_t rk0[10], rk1[10];
+    {
+        uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+#pragma unroll
+        for (int r = 0; r < 10; ++r) { rk0[r] = k0; rk1[r] = k1; k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
+    }
+
+    if (tid < K) {
+        const int e = e0 + tid;
+        const int g = e / per, pos = kind ? b.NT + (e % per) : (e % per);
+        const int clone = b.perm[((size_t)s * b.NR + g) * b.NSLOT + pos];
+        s_lat[tid] = g * b.NSLOT + clone;
+        const double T_k = temperature(b, kind ? b.NT - 1 : pos);
+        // -2 beta log2(e): exp(-beta dE) = 2^(tb t) with dE = 2 t
+        s_tb[tid] = (float)(-2.0 * 1.4426950408889634073599 / T_k);
+        s_flips[tid] = 0u;
+        s_E[tid] = 0.0;
+    }
+    // ---- couplings -> shared memory, packed colour-row layout
+    const float *Jg = b.J + (size_t)s * 3 * Gm::V;
+    if (!Gm::FULL) {
+        for (int i = tid; i < 3 * LB; i += T) Js[i] = 0.f;
+        __syncthreads();
+    }
+    for (int i = tid; i < Gm::V; i += T) {
+        int w, by;
+        site_slot<L>(i, w, by);
+        const int slot = 4 * w + by;
+        Js[slot] = Jg[i];
+        Js[LB + slot] = Jg[Gm::V + i];
+        Js[2 * LB + slot] = Jg[2 * Gm::V + i];
+    }
+    __syncthreads();
+    // ---- spins -> shared memory
+    for (int k = 0; k < K; ++k) {
+        const uint4 *src = reinterpret_cast<const uint4 *>(
+            b.spins + ((size_t)s * b.NLAT + s_lat[k]) * LW);
+        uint4 *dst = reinterpret_cast<uint4 *>(Ss + k * LW);
+        for (int i = tid; i < LW / 4; i += T) dst[i] = src[i];
+    }
+    __syncthreads();
+
+    const int Gt = a.Gt;                 // groups per lattice lane pass (divides G)
+    const int lane_p = tid / Gt, g0 = tid - lane_p * Gt;
+    const int GP = G / Gt;
+    const int kbase = lane_p * KT;       // this thread's lattices: kbase .. kbase+KT-1
+    const bool warp_uniform = (Gt % 32) == 0;
+    uint32_t *Sb = Ss + kbase * LW;
+    unsigned nfl[KT];
+#pragma unroll
+    for (int jj = 0; jj < KT; ++jj) nfl[jj] = 0u;
+
+    for (int sw = 0; sw < nsw; ++sw) {
+        const uint32_t c3base = TAG_SWEEP | ((uint32_t)(sweep_base + sw) << 9);
+        for (int c = 0; c < 2; ++c) {
+            const uint32_t c3 = c3base | ((uint32_t)c << 8);
+            for (int gi = 0; gi < GP; ++gi) {
+                const int g = g0 + gi * Gt;
+                const GroupGeo q = group_geo<L>(g, c);
+                const int j = g % W;
+                const int cc = c ^ 1;
+                const int r = g / W;
+                const int y = r % L, z = r / L;
+                const int rym = ((y + L - 1) % L) + L * z, rzm = y + L * ((z + L - 1) % L);
+                // couplings of the group's 4 sites: +x,-x,+y,-y,+z,-z
+                float Jc[4][6];
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk) {
+                    int m = 4 * j + kk;
+                    if (m >= Lh) m = Lh - 1;
+                    const int so = 4 * q.own + kk;
+                    const int mxm = q.par ? m : (m + Lh - 1) % Lh;
+                    Jc[kk][0] = Js[so];
+                    Jc[kk][1] = Js[4 * ((cc * ROWS + r) * W) + mxm];
+                    Jc[kk][2] = Js[LB + so];
+                    Jc[kk][3] = Js[LB + 4 * ((cc * ROWS + rym) * W) + m];
+                    Jc[kk][4] = Js[2 * LB + so];
+                    Jc[kk][5] = Js[2 * LB + 4 * ((cc * ROWS + rzm) * W) + m];
+                }
+                // flip-mask bits of the real sites of this group
+                uint32_t vmask = 0x80808080u;
+                if (!Gm::FULL) {
+                    const int nv = Lh - 4 * j;
+                    vmask = nv >= 4 ? 0x80808080u : (0x80808080u >> (8 * (4 - nv)));
+                }
+#pragma unroll
+                for (int jj = 0; jj < KT; ++jj) {
+                    const int k = kbase + jj;
+                    if (k >= K) break;
+                    uint32_t *S = Sb + jj * LW;
+                    const uint32_t own = S[q.own];
+                    const uint32_t xa = S[q.xa];
+                    const uint32_t xs = __byte_perm(S[q.wA], S[q.wB], q.selx);
+                    const uint32_t wxp = q.par ? xs : xa, wxm = q.par ? xa : xs;
+                    const uint32_t wyp = S[q.yp], wym = S[q.ym], wzp = S[q.zp], wzm = S[q.zm];
+                    const u4 rnd = philox10_rk((uint32_t)g, (uint32_t)s_lat[k], emcs, c3, rk0, rk1);
+                    const uint32_t rw[4] = {rnd.x, rnd.y, rnd.z, rnd.w};
+                    const float tb = s_tb[k];
+                    uint32_t fm;
+                    if (RULE == PTHR_METROPOLIS) {
+                        // bytes 0x3F where s_i s_j = +1, 0xBF where -1
+                        const uint32_t X = 0x3F3F3F3Fu;
+                        const uint32_t pxp = own ^ wxp ^ X, pxm = own ^ wxm ^ X;
+                        const uint32_t pyp = own ^ wyp ^ X, pym = own ^ wym ^ X;
+                        const uint32_t pzp = own ^ wzp ^ X, pzm = own ^ wzm ^ X;
+                        float dv[4];
+#pragma unroll
+                        for (int kk = 0; kk < 4; ++kk) {
+                            float tt = Jc[kk][0] * spinf(pxp, kk);
+                            tt = fmaf(Jc[kk][1], spinf(pxm, kk), tt);
+                            tt = fmaf(Jc[kk][2], spinf(pyp, kk), tt);
+                            tt = fmaf(Jc[kk][3], spinf(pym, kk), tt);
+                            tt = fmaf(Jc[kk][4], spinf(pzp, kk), tt);
+                            tt = fmaf(Jc[kk][5], spinf(pzm, kk), tt);
+                            const float p = fast_exp2(tb * tt);
+                            // u - p < 0  <=>  accept (u = (x >> 8) 2^-24, exact)
+                            dv[kk] = fmaf(__uint2float_rz(rw[kk] >> 8), 5.9604644775390625e-08f, -p);
+                        }
+                        // sign byte of each difference -> byte kk of the mask
+                        const uint32_t lo = __byte_perm(__float_as_uint(dv[0]), __float_as_uint(dv[1]), 0x0073u);
+                        const uint32_t hi = __byte_perm(__float_as_uint(dv[2]), __float_as_uint(dv[3]), 0x7300u);
+                        fm = __byte_perm(lo, hi, 0x7610u) & vmask;
+                    } else {
+                        fm = 0u;
+#pragma unroll
+                        for (int kk = 0; kk < 4; ++kk) {
+                            const float si = spinf(own, kk);
+                            float h = Jc[kk][0] * spinf(wxp, kk);
+                            h = fmaf(Jc[kk][1], spinf(wxm, kk), h);
+                            h = fmaf(Jc[kk][2], spinf(wyp, kk), h);
+                            h = fmaf(Jc[kk][3], spinf(wym, kk), h);
+                            h = fmaf(Jc[kk][4], spinf(wzp, kk), h);
+                            h = fmaf(Jc[kk][5], spinf(wzm, kk), h);
+                            const float u = uniform24f(rw[kk]);
+                            const float p_up = __frcp_rn(1.f + fast_exp2(tb * h));
+                            const bool flip = (u < p_up) != (si > 0.f);
+                            fm |= flip ? (0x80u << (8 * kk)) : 0u;
+                        }
+                        fm &= vmask;
+                    }
+                    S[q.own] = own ^ fm;
+                    nfl[jj] += __popc(fm);
+                }
+            }
+            __syncthreads();
+        }
+    }
+
+    // ---- energies (Eq. (1)) of the swept lattices: each thread sums the
+    // forward bonds of its sites exactly in FP32 pairs, then FP64 reduction.
+#pragma unroll
+    for (int jj = 0; jj < KT; ++jj) {
+        const int k = kbase + jj;
+        const bool mine = k < K;
+        float hi = 0.f, lo = 0.f;
+        if (mine) {
+            const uint32_t *S = Sb + jj * LW;
+            for (int gi = 0; gi < GP; ++gi) {
+                const int g = g0 + gi * Gt;
+                const int j = g % W;
+                for (int c = 0; c < 2; ++c) {
+                    const GroupGeo q = group_geo<L>(g, c);
+                    const uint32_t own = S[q.own];
+                    const uint32_t xa = S[q.xa];
+                    const uint32_t xs = __byte_perm(S[q.wA], S[q.wB], q.selx);
+                    const uint32_t wxp = q.par ? xs : xa;
+                    const uint32_t wyp = S[q.yp], wzp = S[q.zp];
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk) {
+                        if (!Gm::FULL && 4 * j + kk >= Lh) continue;
+                        const int so = 4 * q.own + kk;
+                        const float si = spinf(own, kk);
+                        two_sum_acc(hi, lo, si * (Js[so] * spinf(wxp, kk)));
+                        two_sum_acc(hi, lo, si * (Js[LB + so] * spinf(wyp, kk)));
+                        two_sum_acc(hi, lo, si * (Js[2 * LB + so] * spinf(wzp, kk)));
+                    }
+                }
+            }
+        }
+        double v = (double)hi + (double)lo;
+        unsigned nf = nfl[jj];
+        if (warp_uniform) {
+            // every lane of a warp has the same lattice lane, hence the same k
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            nf = __reduce_add_sync(0xffffffffu, nf);
+            if ((tid & 31) == 0 && mine) {
+                atomicAdd(&s_E[k], v);
+                atomicAdd(&s_flips[k], nf);
+            }
+        } else if (mine) {
+            atomicAdd(&s_E[k], v);
+            atomicAdd(&s_flips[k], nf);
+        }
+    }
+    __syncthreads();
+    // ---- write back
+    for (int k = 0; k < K; ++k) {
+        uint4 *dst = reinterpret_cast<uint4 *>(b.spins + ((size_t)s * b.NLAT + s_lat[k]) * LW);
+        const uint4 *src = reinterpret_cast<const uint4 *>(Ss + k * LW);
+        for (int i = tid; i < LW / 4; i += T) dst[i] = src[i];
+    }
+    if (tid < K) {
+        const size_t li = (size_t)s * b.NLAT + s_lat[tid];
+        b.E[li] = -s_E[tid];
+        if (s_flips[tid]) atomicAdd(&b.flips[li], (unsigned long long)s_flips[tid]);
+    }
+}
+
+template <int L, int RULE, int KT>
+cudaError_t launch_sweep_tpl(const SweepArgs &a, int blocks, int threads, size_t smem,
+                             cudaStream_t st) {
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = allow_max_dynamic_smem(sweep_kernel<L, RULE, KT>);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    sweep_kernel<L, RULE, KT><<<blocks, threads, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace sweep_detail
+}  // namespace pthr
