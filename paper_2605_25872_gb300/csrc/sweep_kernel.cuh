@@ -77,6 +77,14 @@ __device__ __forceinline__ GroupGeo group_geo(int g, int c) {
     return q;
 }
 
+// 32x32 -> 64-bit product as one wide multiply.
+__device__ __forceinline__ void mul_wide(uint32_t a, uint32_t b, uint32_t &hi, uint32_t &lo) {
+    unsigned long long p;
+    asm("mul.wide.u32 %0, %1, %2;" : "=l"(p) : "r"(a), "r"(b));
+    lo = (uint32_t)p;
+    hi = (uint32_t)(p >> 32);
+}
+
 // Philox4x32-10 with the ten round keys precomputed (the key is the sample
 // seed, the same for the whole block).
 __device__ __forceinline__ u4 philox10_rk(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
@@ -84,13 +92,40 @@ __device__ __forceinline__ u4 philox10_rk(uint32_t c0, uint32_t c1, uint32_t c2,
     const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
-        const uint32_t hi0 = __umulhi(M0, c0), lo0 = M0 * c0;
-        const uint32_t hi1 = __umulhi(M1, c2), lo1 = M1 * c2;
+        uint32_t hi0, lo0, hi1, lo1;
+        mul_wide(M0, c0, hi0, lo0);
+        mul_wide(M1, c2, hi1, lo1);
         const uint32_t n0 = hi1 ^ c1 ^ rk0[r];
         const uint32_t n2 = hi0 ^ c3 ^ rk1[r];
         c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
     }
     return u4{c0, c1, c2, c3};
+}
+
+// Packed FP32 pairs (Blackwell f32x2 arithmetic): two independent IEEE
+// round-to-nearest operations per instruction.
+typedef unsigned long long f2;
+__device__ __forceinline__ f2 pack2(float a, float b) {
+    f2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void unpack2(f2 v, float &a, float &b) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) {
+    f2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ f2 mul2(f2 a, f2 b) {
+    f2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+// spins of sites 2h and 2h+1 of a product word as a packed pair
+__device__ __forceinline__ f2 spin_pair(uint32_t w, int h) {
+    return pack2(spinf(w, 2 * h), spinf(w, 2 * h + 1));
 }
 
 template <int L, int RULE, int KT>
@@ -210,6 +245,13 @@ __global__ void __launch_bounds__(512) sweep_kernel(SweepArgs a) {
                     Jc[kk][4] = Js[2 * LB + so];
                     Jc[kk][5] = Js[2 * LB + 4 * ((cc * ROWS + rzm) * W) + m];
                 }
+                // the same couplings as packed pairs (sites 0,1 and 2,3)
+                f2 Jp[2][6];
+#pragma unroll
+                for (int n = 0; n < 6; ++n) {
+                    Jp[0][n] = pack2(Jc[0][n], Jc[1][n]);
+                    Jp[1][n] = pack2(Jc[2][n], Jc[3][n]);
+                }
                 // flip-mask bits of the real sites of this group
                 uint32_t vmask = 0x80808080u;
                 if (!Gm::FULL) {
@@ -237,17 +279,24 @@ __global__ void __launch_bounds__(512) sweep_kernel(SweepArgs a) {
                         const uint32_t pyp = own ^ wyp ^ X, pym = own ^ wym ^ X;
                         const uint32_t pzp = own ^ wzp ^ X, pzm = own ^ wzm ^ X;
                         float dv[4];
+                        const f2 tb2 = pack2(tb, tb);
+                        const f2 sc2 = pack2(5.9604644775390625e-08f, 5.9604644775390625e-08f);
 #pragma unroll
-                        for (int kk = 0; kk < 4; ++kk) {
-                            float tt = Jc[kk][0] * spinf(pxp, kk);
-                            tt = fmaf(Jc[kk][1], spinf(pxm, kk), tt);
-                            tt = fmaf(Jc[kk][2], spinf(pyp, kk), tt);
-                            tt = fmaf(Jc[kk][3], spinf(pym, kk), tt);
-                            tt = fmaf(Jc[kk][4], spinf(pzp, kk), tt);
-                            tt = fmaf(Jc[kk][5], spinf(pzm, kk), tt);
-                            const float p = fast_exp2(tb * tt);
+                        for (int h = 0; h < 2; ++h) {
+                            // t = sum_j J_ij s_i s_j for sites 2h, 2h+1 (packed)
+                            f2 tt = mul2(Jp[h][0], spin_pair(pxp, h));
+                            tt = fma2(Jp[h][1], spin_pair(pxm, h), tt);
+                            tt = fma2(Jp[h][2], spin_pair(pyp, h), tt);
+                            tt = fma2(Jp[h][3], spin_pair(pym, h), tt);
+                            tt = fma2(Jp[h][4], spin_pair(pzp, h), tt);
+                            tt = fma2(Jp[h][5], spin_pair(pzm, h), tt);
+                            float y0, y1;
+                            unpack2(mul2(tb2, tt), y0, y1);
+                            const f2 negp = pack2(-fast_exp2(y0), -fast_exp2(y1));
                             // u - p < 0  <=>  accept (u = (x >> 8) 2^-24, exact)
-                            dv[kk] = fmaf(__uint2float_rz(rw[kk] >> 8), 5.9604644775390625e-08f, -p);
+                            const f2 u2 = pack2(__uint2float_rz(rw[2 * h] >> 8),
+                                                __uint2float_rz(rw[2 * h + 1] >> 8));
+                            unpack2(fma2(u2, sc2, negp), dv[2 * h], dv[2 * h + 1]);
                         }
                         // sign byte of each difference -> byte kk of the mask
                         const uint32_t lo = __byte_perm(__float_as_uint(dv[0]), __float_as_uint(dv[1]), 0x0073u);
