@@ -413,6 +413,62 @@ def end_to_end(dev, cfg, J, seeds, steps):
                         f"{steps} EMCS, D2H observables after every EMCS"}
 
 
+def run_serve(args):
+    """Serving: Poisson stream of single-sample requests with L uniform in
+    {6, 8, 10, 12, 16} (24 temperatures 0.2..1.6, 4 replicas + 4 reservoir
+    clones, paper EMCS), admitted into per-L resident pools sized from a
+    device-memory budget; rate = 0.8 x the measured capacity."""
+    import torch
+    from paper_2605_25872_gb300.build import build
+    from paper_2605_25872_gb300 import required_bytes, BatchConfig
+    from paper_2605_25872_gb300.serve import PoolSpec, Request, Server
+    build()
+    torch.cuda.set_device(0)
+    budget = args.serve_budget
+    mem = args.serve_mem_gb * 1e9
+    specs = []
+    for L in W.SERVE_SIZES:
+        one = required_bytes(BatchConfig(L=L, n_samples=1, n_temps=24))
+        slots = int(min(args.serve_max_slots, (mem / len(W.SERVE_SIZES)) // one))
+        specs.append(PoolSpec(L=L, slots=slots, n_temps=24))
+    # capacity probe: every pool full, EMCS steps timed with all pools in flight
+    srv = Server(specs)
+    probe = [Request(rid=-1 - i * 100000 - k, L=sp.L, seed=10 ** 6 + i * 100000 + k, budget_emcs=10 ** 6)
+             for i, sp in enumerate(specs) for k in range(sp.slots)]
+    per_emcs_s = srv.fill_and_time(probe, 5)
+    del srv
+    torch.cuda.synchronize()
+    cap = min(sp.slots / (budget * per_emcs_s) for sp in specs) * len(specs)   # requests/s
+    lam = 0.8 * cap
+    n_req = args.serve_requests
+    times, Ls = W.poisson_arrivals(n_req, lam, W.batch_seed(5))
+    reqs = [Request(rid=i, L=int(Ls[i]), seed=W.batch_seed(5) + 7919 * i, budget_emcs=budget,
+                    arrival=float(times[i])) for i in range(n_req)]
+    srv = Server(specs)
+    srv.run(reqs, realtime=True)
+    st = srv.stats()
+    line = {"mode": "serve", "metric": "time-to-budget p50/p99 and aggregate spin updates/ns",
+            "p50_s": st["p50_s"], "p99_s": st["p99_s"], "updates_per_ns": st["updates_per_ns"],
+            "requests": st["requests"], "budget_emcs": budget, "lambda_per_s": lam,
+            "capacity_per_s": cap, "full_pool_emcs_s": per_emcs_s, "slots": {sp.L: sp.slots for sp in specs},
+            "memory_budget_gb": args.serve_mem_gb, "emcs_steps": st["emcs_steps"],
+            "config": {"workload": "serving: L uniform in {6,8,10,12,16}, 24 T 0.2..1.6, 4 replicas + "
+                                   "4 reservoir clones, paper EMCS, couplings drawn on the device from each "
+                                   "request's seed, 960-sweep reservoir pre-thermalisation at admission"}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_autotune(args):
+    from paper_2605_25872_gb300.build import build
+    from paper_2605_25872_gb300.autotune import autotune
+    build()
+    cfg = batch_config(args.samples)
+    shape = autotune(cfg, emcs=3, use_cache=False, verbose=True)
+    print(json.dumps({"mode": "autotune", "best": shape}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -423,7 +479,17 @@ def main():
                     help="samples per GPU (profiling cases only; the headline uses 512)")
     ap.add_argument("--no-extras", action="store_true",
                     help="time the batched EMCS only (no plain form, e2e, CPU baseline)")
+    ap.add_argument("--serve", action="store_true", help="serving mode (separate JSON line)")
+    ap.add_argument("--serve-budget", type=int, default=100, help="EMCS per request (serving)")
+    ap.add_argument("--serve-requests", type=int, default=200)
+    ap.add_argument("--serve-mem-gb", type=float, default=2.0)
+    ap.add_argument("--serve-max-slots", type=int, default=128)
+    ap.add_argument("--autotune", action="store_true", help="print the shape sweep for the workload")
     args = ap.parse_args()
+    if args.serve:
+        return run_serve(args)
+    if args.autotune:
+        return run_autotune(args)
     if args.warmup < 3 and args.impl != "reference":
         args.warmup = 3
     if args.impl == "reference":

@@ -123,7 +123,10 @@ typedef struct {
     int pt_lattices_per_block;    /* lattices of one sample per sweep block, PT      */
     int res_lattices_per_block;   /* same for reservoir clones                       */
     int sweep_threads;            /* threads per sweep block (multiple of the work)  */
-    int cluster_threads;          /* threads per cluster-move block                  */
+    int cluster_threads;          /* threads per cluster-move block (<= 512)         */
+    int cluster_iter_cap;         /* 0: automatic bound 4V+64 on every union-find
+                                     loop; a small value exercises the bounded-loop
+                                     error path (PTHR_E_NOCONVERGE, spins unchanged) */
 } pthr_tuning;
 
 /* Total workspace bytes for cfg (every sub-buffer 256-byte aligned).

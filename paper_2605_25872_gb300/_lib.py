@@ -45,7 +45,8 @@ class Config(ctypes.Structure):
 
 class Tuning(ctypes.Structure):
     _fields_ = [("pt_lattices_per_block", ctypes.c_int), ("res_lattices_per_block", ctypes.c_int),
-                ("sweep_threads", ctypes.c_int), ("cluster_threads", ctypes.c_int)]
+                ("sweep_threads", ctypes.c_int), ("cluster_threads", ctypes.c_int),
+                ("cluster_iter_cap", ctypes.c_int)]
 
 
 class PthrError(RuntimeError):

@@ -1,0 +1,105 @@
+"""Autotuner for the kernel shapes of a batch configuration.
+
+It times whole EMCS (CUDA events on the batch's stream) for candidate shapes:
+lattices per sweep block for PT and reservoir clones, sweep threads, and
+cluster threads.  It does this on a scratch batch of the same configuration,
+keeps the fastest shape, and caches it per (configuration, GPU).  Shapes
+never change results, because every random number is keyed by (sample,
+lattice, site, step), so tuning can run on synthetic couplings and the
+winner can be applied to any batch of that configuration.
+"""
+from __future__ import annotations
+
+import itertools
+import json
+import os
+
+import numpy as np
+
+from ._lib import PthrError
+from .batch import Batch, BatchConfig
+
+CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "tuning_cache.json")
+
+
+def _key(cfg: BatchConfig, device_name: str) -> str:
+    d = dict(cfg.__dict__)
+    d.pop("seed", None)
+    return device_name + "|" + json.dumps(d, sort_keys=True)
+
+
+def candidates(cfg: BatchConfig):
+    npt = cfg.n_replicas * cfg.n_temps
+    nres = cfg.n_replicas * max(cfg.n_res, 1)
+    ks = sorted({k for k in (4, 8, 12, 16, 24, 32, 48, 64) if k <= npt} | {npt if npt <= 64 else 64})
+    kr = sorted({k for k in (2, 4, 8, 16, 32) if k <= nres} | {nres if nres <= 64 else 64})
+    for kp, krs in itertools.product(ks, kr):
+        yield {"pt_lattices_per_block": kp, "res_lattices_per_block": krs}
+    for ct in (128, 256):
+        yield {"cluster_threads": ct}
+
+
+def time_shape(b: Batch, shape: dict, emcs: int = 3, warmup: int = 1) -> float:
+    import torch
+    b.set_tuning(**shape)
+    b.emcs(warmup)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(b.stream):
+        e0.record(b.stream)
+        b.emcs(emcs)
+        e1.record(b.stream)
+    b.stream.synchronize()
+    return e0.elapsed_time(e1) / emcs
+
+
+def autotune(cfg: BatchConfig, emcs: int = 3, use_cache: bool = True, device="cuda",
+             verbose: bool = False) -> dict:
+    """Return the fastest shape for cfg (measured on this GPU)."""
+    import torch
+    name = torch.cuda.get_device_name(torch.device(device))
+    key = _key(cfg, name)
+    cache = {}
+    if use_cache and os.path.exists(CACHE):
+        with open(CACHE) as f:
+            cache = json.load(f)
+        if key in cache:
+            return cache[key]["shape"]
+    rng = np.random.default_rng(0)
+    J = np.rint(rng.standard_normal((cfg.n_samples, 3, cfg.L ** 3)) * 2 ** 18) / 2 ** 18
+    b = Batch(cfg, couplings=J.astype(np.float32), device=device)
+    base = time_shape(b, {}, emcs)
+    best, best_ms = {}, base
+    results = [({}, base)]
+    sweep_best = {}
+    for shape in candidates(cfg):
+        trial = dict(sweep_best)
+        trial.update(shape)
+        try:
+            ms = time_shape(b, trial, emcs)
+        except PthrError:
+            continue
+        results.append((trial, ms))
+        if verbose:
+            print(f"{trial}: {ms:.3f} ms/EMCS")
+        if ms < best_ms:
+            best, best_ms = trial, ms
+            if "pt_lattices_per_block" in shape:
+                sweep_best = {k: v for k, v in trial.items() if k != "cluster_threads"}
+    b.close()
+    entry = {"shape": best, "ms_per_emcs": best_ms, "default_ms_per_emcs": base,
+             "tried": len(results)}
+    if use_cache:
+        os.makedirs(os.path.dirname(CACHE), exist_ok=True)
+        cache[key] = entry
+        with open(CACHE, "w") as f:
+            json.dump(cache, f, indent=1)
+    return best
+
+
+def tuned_batch(cfg: BatchConfig, **kw) -> Batch:
+    """A batch with the autotuned shape applied."""
+    shape = autotune(cfg, device=kw.get("device", "cuda"))
+    b = Batch(cfg, **kw)
+    if shape:
+        b.set_tuning(**shape)
+    return b

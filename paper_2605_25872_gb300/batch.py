@@ -250,8 +250,9 @@ class Batch:
         check(self.lib.pthr_set_active(self.h, first, count, int(active)), self.h)
 
     def set_tuning(self, pt_lattices_per_block=0, res_lattices_per_block=0, sweep_threads=0,
-                   cluster_threads=0):
-        t = _lib.Tuning(pt_lattices_per_block, res_lattices_per_block, sweep_threads, cluster_threads)
+                   cluster_threads=0, cluster_iter_cap=0):
+        t = _lib.Tuning(pt_lattices_per_block, res_lattices_per_block, sweep_threads, cluster_threads,
+                        cluster_iter_cap)
         check(self.lib.pthr_set_tuning(self.h, ctypes.byref(t)), self.h)
 
     def get_tuning(self) -> dict:

@@ -227,7 +227,8 @@ pthr_status do_cluster(pthr_batch *b, int label_only, int32_t *labels) {
     a.sample_count = b->cfg.n_samples;
     a.label_only = label_only;
     a.labels_out = labels;
-    int threads = b->tuning.cluster_threads > 0 ? b->tuning.cluster_threads : 512;
+    a.iter_cap = b->tuning.cluster_iter_cap;
+    int threads = b->tuning.cluster_threads > 0 ? b->tuning.cluster_threads : 256;
     const int V = b->cfg.L * b->cfg.L * b->cfg.L;
     if (threads > ((V + 31) / 32) * 32) threads = ((V + 31) / 32) * 32;
     if (threads < 32) threads = 32;
@@ -382,7 +383,8 @@ PTHR_API pthr_status pthr_set_tuning(pthr_batch *b, const pthr_tuning *t) {
     if (t) nt = *t;
     if (nt.pt_lattices_per_block < 0 || nt.pt_lattices_per_block > sweep_max_k() ||
         nt.res_lattices_per_block < 0 || nt.res_lattices_per_block > sweep_max_k() ||
-        nt.sweep_threads < 0 || nt.sweep_threads > 512 || nt.cluster_threads < 0 || nt.cluster_threads > 512)
+        nt.sweep_threads < 0 || nt.sweep_threads > 512 || nt.cluster_threads < 0 || nt.cluster_threads > 512 ||
+        nt.cluster_iter_cap < 0)
         return fail(b, PTHR_E_INVAL, "tuning out of range");
     pthr_tuning old = b->tuning;
     b->tuning = nt;
@@ -404,7 +406,8 @@ PTHR_API pthr_status pthr_get_tuning(const pthr_batch *b, pthr_tuning *t) {
     t->pt_lattices_per_block = sh.K_pt;
     t->res_lattices_per_block = sh.K_res;
     t->sweep_threads = sh.threads;
-    t->cluster_threads = b->tuning.cluster_threads > 0 ? b->tuning.cluster_threads : 512;
+    t->cluster_threads = b->tuning.cluster_threads > 0 ? b->tuning.cluster_threads : 256;
+    t->cluster_iter_cap = b->tuning.cluster_iter_cap;
     return PTHR_OK;
 }
 

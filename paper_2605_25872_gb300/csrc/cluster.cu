@@ -106,7 +106,7 @@ __global__ void __launch_bounds__(512) cluster_kernel(ClusterArgs a) {
     }
     __syncthreads();
     bool ok = true;
-    const int cap = 4 * V + 64;
+    const int cap = a.iter_cap > 0 ? a.iter_cap : 4 * V + 64;
     volatile int *vp = parent;
     for (int i = tid; i < V; i += T) {
         const unsigned char qi = flag[i];

@@ -29,6 +29,7 @@ struct ClusterArgs {
     int sample_first, sample_count;
     int label_only;          // 1: only write labels (no flip, no energies)
     int32_t *labels_out;     // optional [S][NPAIR][NT][V] canonical labels
+    int iter_cap;            // bound on every union-find loop (> 0)
 };
 cudaError_t launch_cluster(const ClusterArgs &a, int threads, cudaStream_t st);
 size_t cluster_smem_bytes_for(int L);

@@ -1,0 +1,229 @@
+"""Continuous-batching request loop for PTHR samples of mixed lattice size.
+
+A request is one disorder sample (couplings, seed, lattice size L) that needs
+a fixed budget of EMCS.  The server keeps one resident batch ("pool") per
+lattice size, each on its own CUDA stream.  It admits waiting requests into
+free slots whenever a slot frees up (by device memory: the pools are sized
+from a memory budget).  It advances every pool that has work by one EMCS at
+a time, so pools overlap on the device.  It reads a request's observables
+back when its budget is done, then frees the slot.
+
+Because every random number is keyed by the request's own seed and
+EMCS counter, a request's result is the same whether it runs alone or in a
+busy pool; the tests check this bit for bit.
+"""
+from __future__ import annotations
+
+import time
+from collections import deque
+from dataclasses import dataclass, field
+
+import numpy as np
+
+
+@dataclass
+class Request:
+    rid: int
+    L: int
+    seed: int
+    budget_emcs: int
+    arrival: float = 0.0                  # seconds since the start of the run
+    couplings: np.ndarray | None = None   # FP32 [3, V]; None: drawn on the device from seed
+    # filled by the server
+    admitted: float | None = None
+    finished: float | None = None
+    obs: np.ndarray | None = None         # accumulators [n_temps, 8]
+    round_trips: np.ndarray | None = None
+
+    @property
+    def latency(self):
+        return None if self.finished is None else self.finished - self.arrival
+
+
+@dataclass
+class PoolSpec:
+    L: int
+    slots: int
+    n_temps: int = 24
+    t_min: float = 0.2
+    t_max: float = 1.6
+    n_replicas: int = 4
+    n_res: int = 4
+    sweeps_per_emcs: int = 10
+    res_sweeps_per_emcs: int = 240
+    pretherm_sweeps: int = 960
+
+    def updates_per_emcs_per_sample(self):
+        V = self.L ** 3
+        return self.n_replicas * (self.n_temps * self.sweeps_per_emcs
+                                  + self.n_res * self.res_sweeps_per_emcs) * V
+
+
+class GpuPool:
+    """One resident batch of `spec.slots` samples of one lattice size."""
+
+    def __init__(self, spec: PoolSpec, device="cuda", graph=True):
+        import torch
+        from .batch import Batch, BatchConfig
+        self.spec = spec
+        self.stream = torch.cuda.Stream(device)
+        self.cfg = BatchConfig(L=spec.L, n_samples=spec.slots, n_temps=spec.n_temps,
+                               t_min=spec.t_min, t_max=spec.t_max, n_replicas=spec.n_replicas,
+                               n_res=spec.n_res, sweeps_per_emcs=spec.sweeps_per_emcs,
+                               res_sweeps_per_emcs=spec.res_sweeps_per_emcs,
+                               er_on=spec.n_res > 0, cluster="acu")
+        self.batch = Batch(self.cfg, device=device, stream=self.stream)
+        self.batch.set_active(0, spec.slots, False)
+        self.graph = graph
+        self.host_obs = np.zeros((spec.slots, spec.n_temps, 8))
+
+    def reset(self, slot, req: Request):
+        self.reset_many([slot], [req])
+
+    def reset_many(self, slots, reqs):
+        """Admit requests into slots; consecutive slots whose couplings are all
+        given (or all drawn from seeds) share one call, so their reservoir
+        pre-thermalisation runs as one launch."""
+        order = sorted(range(len(slots)), key=lambda i: slots[i])
+        run = []
+
+        def flush():
+            if not run:
+                return
+            first = slots[run[0]]
+            seeds = [reqs[i].seed for i in run]
+            cpl = None
+            if reqs[run[0]].couplings is not None:
+                cpl = np.ascontiguousarray(np.stack([reqs[i].couplings for i in run]), np.float32)
+            self.batch.reset_samples(first, len(run), seeds=seeds, couplings=cpl,
+                                     pretherm_sweeps=self.spec.pretherm_sweeps)
+            run.clear()
+
+        for i in order:
+            if run and (slots[i] != slots[run[-1]] + 1
+                        or (reqs[i].couplings is None) != (reqs[run[0]].couplings is None)):
+                flush()
+            run.append(i)
+        flush()
+
+    def step(self):
+        self.batch.emcs(1, graph=self.graph)
+
+    def wait(self):
+        self.stream.synchronize()
+
+    def read(self, slot):
+        obs = self.batch.obs[slot].cpu().numpy().copy()
+        trips = self.batch.round_trips[slot].cpu().numpy().copy()
+        return obs, trips
+
+    def free(self, slot):
+        self.batch.set_active(slot, 1, False)
+
+
+class Server:
+    """Admission queue -> slots -> EMCS steps -> completion -> readback."""
+
+    def __init__(self, specs, pool_factory=None, clock=None):
+        self.specs = {s.L: s for s in specs}
+        self.pool_factory = pool_factory or (lambda spec: GpuPool(spec))
+        self.pools = {L: self.pool_factory(s) for L, s in self.specs.items()}
+        self.slot_req = {L: [None] * s.slots for L, s in self.specs.items()}
+        self.remaining = {L: np.zeros(s.slots, dtype=np.int64) for L, s in self.specs.items()}
+        self.queue = {L: deque() for L in self.specs}
+        self.done = []
+        self.clock = clock or time.perf_counter
+        self.t0 = None
+        self.emcs_steps = {L: 0 for L in self.specs}
+
+    def now(self):
+        return self.clock() - self.t0
+
+    def submit(self, req: Request):
+        if req.L not in self.specs:
+            raise ValueError(f"no pool for L={req.L}")
+        self.queue[req.L].append(req)
+
+    def _admit(self):
+        for L, q in self.queue.items():
+            slots = self.slot_req[L]
+            free = [i for i, r in enumerate(slots) if r is None]
+            take = []
+            while q and free:
+                take.append((free.pop(0), q.popleft()))
+            if not take:
+                continue
+            pool = self.pools[L]
+            if hasattr(pool, "reset_many"):
+                pool.reset_many([s for s, _ in take], [r for _, r in take])
+            else:
+                for s, r in take:
+                    pool.reset(s, r)
+            t = self.now()
+            for slot, req in take:
+                req.admitted = t
+                slots[slot] = req
+                self.remaining[L][slot] = req.budget_emcs
+
+    def fill_and_time(self, requests, n_emcs):
+        """Capacity probe: admit `requests` (filling the pools), then time
+        n_emcs steps of every busy pool (admission excluded)."""
+        self.t0 = self.clock()
+        for r in requests:
+            self.submit(r)
+        self._admit()
+        for p in self.pools.values():
+            p.wait()
+        t0 = self.clock()
+        for _ in range(n_emcs):
+            self._step_all()
+        return (self.clock() - t0) / n_emcs
+
+    def busy(self):
+        return any(r is not None for sl in self.slot_req.values() for r in sl)
+
+    def _step_all(self):
+        stepped = [L for L, sl in self.slot_req.items() if any(r is not None for r in sl)]
+        for L in stepped:                 # enqueue one EMCS per busy pool (streams overlap)
+            self.pools[L].step()
+            self.emcs_steps[L] += 1
+        for L in stepped:
+            self.pools[L].wait()
+            rem = self.remaining[L]
+            for slot, req in enumerate(self.slot_req[L]):
+                if req is None:
+                    continue
+                rem[slot] -= 1
+                if rem[slot] == 0:
+                    req.obs, req.round_trips = self.pools[L].read(slot)
+                    req.finished = self.now()
+                    self.pools[L].free(slot)
+                    self.slot_req[L][slot] = None
+                    self.done.append(req)
+
+    def run(self, requests, realtime=True):
+        """Serve `requests` (sorted by arrival).  With realtime=True arrivals
+        follow the wall clock; otherwise every request is queued at once."""
+        pending = deque(sorted(requests, key=lambda r: r.arrival))
+        self.t0 = self.clock()
+        while pending or self.busy() or any(self.queue.values()):
+            now = self.now()
+            while pending and (not realtime or pending[0].arrival <= now):
+                self.submit(pending.popleft())
+            self._admit()
+            if self.busy():
+                self._step_all()
+            elif pending:
+                time.sleep(max(0.0, min(0.001, pending[0].arrival - self.now())))
+        return self.done
+
+    def stats(self):
+        lat = np.array([r.latency for r in self.done])
+        upd = sum(self.specs[r.L].updates_per_emcs_per_sample() * r.budget_emcs for r in self.done)
+        span = max(r.finished for r in self.done) if self.done else 0.0
+        return {"requests": len(self.done),
+                "p50_s": float(np.percentile(lat, 50)) if len(lat) else None,
+                "p99_s": float(np.percentile(lat, 99)) if len(lat) else None,
+                "makespan_s": span,
+                "updates_per_ns": upd / (span * 1e9) if span > 0 else None,
+                "emcs_steps": dict(self.emcs_steps)}

@@ -414,3 +414,37 @@ def test_status_word_reads_ok():
     b = Batch(cfg, couplings=W.gaussian_couplings(8, 2, 1), seeds=W.sample_seeds(2, 2))
     b.emcs(3)
     assert b.poll(10000) == 0
+
+
+def test_bounded_cluster_loop_reports_noconverge_without_changing_spins():
+    """Failure detection without a fault: an iteration cap of 1 makes the
+    union-find give up; the kernel latches PTHR_E_NOCONVERGE, returns, leaves
+    the spins alone, and the context stays usable."""
+    from paper_2605_25872_gb300 import _lib
+    cfg = BatchConfig(L=8, n_samples=2, n_temps=6, n_replicas=4, n_res=2, sweeps_per_emcs=1,
+                      res_sweeps_per_emcs=2)
+    b = Batch(cfg, couplings=W.gaussian_couplings(8, 2, 3), seeds=W.sample_seeds(4, 2))
+    b.sweep(3, 3)
+    before = gpu_spins(b)
+    e_before = b.energies.cpu().numpy().copy()
+    b.set_tuning(cluster_iter_cap=1)
+    b.houdayer()
+    assert b.poll(10000) == _lib.PTHR_E_NOCONVERGE
+    np.testing.assert_array_equal(gpu_spins(b), before)
+    np.testing.assert_array_equal(b.energies.cpu().numpy(), e_before)
+    b.set_tuning()
+    b.houdayer()
+    assert b.poll(10000) == 0
+
+
+def test_autotuner_returns_a_valid_faster_or_default_shape():
+    from paper_2605_25872_gb300.autotune import autotune
+    cfg = BatchConfig(L=8, n_samples=8, n_temps=8, n_replicas=4, n_res=2, sweeps_per_emcs=2,
+                      res_sweeps_per_emcs=4)
+    shape = autotune(cfg, emcs=2, use_cache=False)
+    J = W.gaussian_couplings(8, 8, 2)
+    a = Batch(cfg, couplings=J, seeds=W.sample_seeds(3, 8))
+    b = Batch(cfg, couplings=J, seeds=W.sample_seeds(3, 8), tuning=shape or None)
+    a.emcs(3)
+    b.emcs(3)
+    _same(_state(a), _state(b))

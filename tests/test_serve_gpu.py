@@ -1,0 +1,57 @@
+"""Serving on the GPU: requests of mixed L admitted into busy pools give the
+same result as the same request run alone."""
+import numpy as np
+import pytest
+import torch
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+P = pytest.importorskip("paper_2605_25872_gb300")
+from paper_2605_25872_gb300 import Batch, BatchConfig  # noqa: E402
+from paper_2605_25872_gb300.build import build  # noqa: E402
+from paper_2605_25872_gb300.serve import PoolSpec, Request, Server  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    build()
+
+
+def alone(spec, req):
+    cfg = BatchConfig(L=spec.L, n_samples=1, n_temps=spec.n_temps, t_min=spec.t_min,
+                      t_max=spec.t_max, n_replicas=spec.n_replicas, n_res=spec.n_res,
+                      sweeps_per_emcs=spec.sweeps_per_emcs,
+                      res_sweeps_per_emcs=spec.res_sweeps_per_emcs, er_on=True, cluster="acu")
+    b = Batch(cfg, couplings=None if req.couplings is None else req.couplings[None],
+              seeds=[req.seed])
+    b.prethermalize(spec.pretherm_sweeps)
+    b.emcs(req.budget_emcs)
+    return b.obs[0].cpu().numpy(), b.round_trips[0].cpu().numpy()
+
+
+def test_serving_result_alone_equals_in_the_mix():
+    specs = [PoolSpec(L=6, slots=3, n_temps=8, sweeps_per_emcs=2, res_sweeps_per_emcs=6,
+                      pretherm_sweeps=12),
+             PoolSpec(L=8, slots=2, n_temps=8, sweeps_per_emcs=2, res_sweeps_per_emcs=6,
+                      pretherm_sweeps=12)]
+    srv = Server(specs)
+    rng = np.random.default_rng(5)
+    reqs = []
+    for i in range(10):
+        L = 6 if i % 2 else 8
+        cpl = W.gaussian_couplings(L, 1, 500 + i)[0] if i % 3 else None
+        reqs.append(Request(rid=i, L=L, seed=9000 + i, budget_emcs=int(rng.integers(3, 9)),
+                            arrival=0.0, couplings=cpl))
+    done = srv.run(reqs, realtime=False)
+    assert len(done) == 10
+    for r in done:
+        spec = srv.specs[r.L]
+        obs, trips = alone(spec, r)
+        np.testing.assert_array_equal(r.obs, obs)
+        np.testing.assert_array_equal(r.round_trips, trips)
+    st = srv.stats()
+    assert st["p50_s"] > 0 and st["updates_per_ns"] > 0
