@@ -69,7 +69,8 @@ typedef enum {
 enum { PTHR_METROPOLIS = 0, PTHR_HEATBATH = 1 };
 enum { PTHR_CLUSTER_OFF = 0, PTHR_CLUSTER_ACU = 1, PTHR_CLUSTER_SINGLE = 2 };
 enum { PTHR_SWAP_PT = 1, PTHR_SWAP_ER = 2 };
-enum { PTHR_OBS_MEASURE = 1, PTHR_OBS_READ_HOST = 2, PTHR_OBS_READ_DEVICE = 4, PTHR_OBS_RESET = 8 };
+enum { PTHR_OBS_MEASURE = 1, PTHR_OBS_READ_HOST = 2, PTHR_OBS_READ_DEVICE = 4, PTHR_OBS_RESET = 8,
+       PTHR_OBS_CHAOS = 16 };
 
 /* Workspace sub-buffers (pthr_buffer_info).  Layouts:
  *  J      float    [S][3][V]        couplings, natural site order
@@ -92,12 +93,16 @@ enum { PTHR_OBS_MEASURE = 1, PTHR_OBS_READ_HOST = 2, PTHR_OBS_READ_DEVICE = 4, P
  *  CSTAT  int64    [S][n_pairs][n_temps][4] cluster statistics of the last
  *                                   cluster move: clusters, largest, second
  *                                   largest, sites flipped
+ *  CHAOS  double   [S][n_temps][2]  temperature-chaos accumulators: count and
+ *                                   sum over pairs of q^2 between the clone of
+ *                                   group 2p at T_0 and the clone of group 2p+1
+ *                                   at T_k (Sec. 5, chaotic parameter)
  */
 enum {
     PTHR_BUF_J = 0, PTHR_BUF_SPINS, PTHR_BUF_ENERGY, PTHR_BUF_PERM, PTHR_BUF_AGE,
     PTHR_BUF_RT, PTHR_BUF_TRIPS, PTHR_BUF_PTACC, PTHR_BUF_FLIPS, PTHR_BUF_OBS,
     PTHR_BUF_EMCS, PTHR_BUF_SEEDS, PTHR_BUF_ACTIVE, PTHR_BUF_STATUS, PTHR_BUF_CSTAT,
-    PTHR_NBUF
+    PTHR_BUF_CHAOS, PTHR_NBUF
 };
 
 typedef struct {
@@ -203,7 +208,10 @@ PTHR_API pthr_status pthr_swap(pthr_batch *b, int flags);
  * temperature) to the OBS accumulators; PTHR_OBS_READ_HOST (host out) or
  * PTHR_OBS_READ_DEVICE (device out) copies the accumulators, double
  * [S][n_temps][PTHR_NOBS], into out (bytes must be >= that size; a host
- * read synchronises the stream); PTHR_OBS_RESET zeroes them afterwards. */
+ * read synchronises the stream); PTHR_OBS_RESET zeroes them afterwards.
+ * PTHR_OBS_CHAOS (with MEASURE) also adds, for every T_k, q^2 between the
+ * T_0 clone of group 2p and the T_k clone of group 2p+1 to the CHAOS buffer
+ * (reset with the other accumulators). */
 PTHR_API pthr_status pthr_observables(pthr_batch *b, int flags, void *out, size_t bytes);
 
 /* n full EMCS: pthr_sweep(sweeps_per_emcs, er_on ? res_sweeps_per_emcs : 0),

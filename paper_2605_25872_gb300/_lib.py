@@ -18,11 +18,11 @@ STATUS_NAMES = {0: "PTHR_OK", 1: "PTHR_E_INVAL", 2: "PTHR_E_NOMEM", 3: "PTHR_E_C
 METROPOLIS, HEATBATH = 0, 1
 CLUSTER_OFF, CLUSTER_ACU, CLUSTER_SINGLE = 0, 1, 2
 SWAP_PT, SWAP_ER = 1, 2
-OBS_MEASURE, OBS_READ_HOST, OBS_READ_DEVICE, OBS_RESET = 1, 2, 4, 8
+OBS_MEASURE, OBS_READ_HOST, OBS_READ_DEVICE, OBS_RESET, OBS_CHAOS = 1, 2, 4, 8, 16
 NOBS = 8
 MAX_L = 24
 (BUF_J, BUF_SPINS, BUF_ENERGY, BUF_PERM, BUF_AGE, BUF_RT, BUF_TRIPS, BUF_PTACC, BUF_FLIPS,
- BUF_OBS, BUF_EMCS, BUF_SEEDS, BUF_ACTIVE, BUF_STATUS, BUF_CSTAT, NBUF) = range(16)
+ BUF_OBS, BUF_EMCS, BUF_SEEDS, BUF_ACTIVE, BUF_STATUS, BUF_CSTAT, BUF_CHAOS, NBUF) = range(17)
 
 # every exported entry point of include/pthr.h
 EXPORTS = ("pthr_required_bytes", "pthr_buffer_info", "pthr_lattice_bytes", "pthr_create_batch",

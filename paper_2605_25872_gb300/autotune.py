@@ -29,13 +29,14 @@ def _key(cfg: BatchConfig, device_name: str) -> str:
 
 
 def candidates(cfg: BatchConfig):
+    """Sweep shapes (PT / reservoir lattices per block), then cluster threads."""
     npt = cfg.n_replicas * cfg.n_temps
     nres = cfg.n_replicas * max(cfg.n_res, 1)
     ks = sorted({k for k in (4, 8, 12, 16, 24, 32, 48, 64) if k <= npt} | {npt if npt <= 64 else 64})
     kr = sorted({k for k in (2, 4, 8, 16, 32) if k <= nres} | {nres if nres <= 64 else 64})
     for kp, krs in itertools.product(ks, kr):
         yield {"pt_lattices_per_block": kp, "res_lattices_per_block": krs}
-    for ct in (128, 256):
+    for ct in (128, 256, 384):
         yield {"cluster_threads": ct}
 
 
@@ -53,8 +54,11 @@ def time_shape(b: Batch, shape: dict, emcs: int = 3, warmup: int = 1) -> float:
 
 
 def autotune(cfg: BatchConfig, emcs: int = 3, use_cache: bool = True, device="cuda",
-             verbose: bool = False) -> dict:
-    """Return the fastest shape for cfg (measured on this GPU)."""
+             verbose: bool = False, warm_emcs: int = 20, pretherm_sweeps: int = 960) -> dict:
+    """Return the fastest shape for cfg (measured on this GPU).  The scratch
+    batch is brought to a representative state first (reservoir
+    pre-thermalisation and warm_emcs EMCS): the cluster step's cost depends on
+    the cluster structure of the replica pairs."""
     import torch
     name = torch.cuda.get_device_name(torch.device(device))
     key = _key(cfg, name)
@@ -67,6 +71,9 @@ def autotune(cfg: BatchConfig, emcs: int = 3, use_cache: bool = True, device="cu
     rng = np.random.default_rng(0)
     J = np.rint(rng.standard_normal((cfg.n_samples, 3, cfg.L ** 3)) * 2 ** 18) / 2 ** 18
     b = Batch(cfg, couplings=J.astype(np.float32), device=device)
+    if cfg.er_on and cfg.n_res:
+        b.prethermalize(pretherm_sweeps)
+    b.emcs(warm_emcs)
     base = time_shape(b, {}, emcs)
     best, best_ms = {}, base
     results = [({}, base)]

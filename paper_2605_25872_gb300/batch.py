@@ -181,6 +181,11 @@ class Batch:
         c = self.cfg
         return self._view(_lib.BUF_CSTAT, torch.int64, (c.n_samples, max(c.n_replicas // 2, 1), c.n_temps, 4))
 
+    @property
+    def chaos(self):
+        c = self.cfg
+        return self._view(_lib.BUF_CHAOS, torch.float64, (c.n_samples, c.n_temps, 2))
+
     # ------------------------------------------------------------------ steps
     def sweep(self, n_pt: int, n_res: int = 0):
         check(self.lib.pthr_sweep(self.h, n_pt, n_res), self.h)
@@ -193,8 +198,9 @@ class Batch:
             er = self.cfg.er_on
         check(self.lib.pthr_swap(self.h, (_lib.SWAP_PT if pt else 0) | (_lib.SWAP_ER if er else 0)), self.h)
 
-    def measure(self):
-        check(self.lib.pthr_observables(self.h, _lib.OBS_MEASURE, None, 0), self.h)
+    def measure(self, chaos: bool = False):
+        flags = _lib.OBS_MEASURE | (_lib.OBS_CHAOS if chaos else 0)
+        check(self.lib.pthr_observables(self.h, flags, None, 0), self.h)
 
     def read_observables(self, out: np.ndarray | None = None) -> np.ndarray:
         """Copy the accumulators to host memory (synchronises the stream)."""

@@ -122,6 +122,7 @@ Layout make_layout(const pthr_config *c) {
     l.len[PTHR_BUF_ACTIVE] = S;
     l.len[PTHR_BUF_STATUS] = 4 * sizeof(uint32_t);
     l.len[PTHR_BUF_CSTAT] = S * NP * NT * 4 * sizeof(long long);
+    l.len[PTHR_BUF_CHAOS] = S * NT * 2 * sizeof(double);
     size_t o = 0;
     for (int i = 0; i < PTHR_NBUF; ++i) {
         l.off[i] = o;
@@ -228,7 +229,7 @@ pthr_status do_cluster(pthr_batch *b, int label_only, int32_t *labels) {
     a.label_only = label_only;
     a.labels_out = labels;
     a.iter_cap = b->tuning.cluster_iter_cap;
-    int threads = b->tuning.cluster_threads > 0 ? b->tuning.cluster_threads : 256;
+    int threads = b->tuning.cluster_threads > 0 ? b->tuning.cluster_threads : 512;
     const int V = b->cfg.L * b->cfg.L * b->cfg.L;
     if (threads > ((V + 31) / 32) * 32) threads = ((V + 31) / 32) * 32;
     if (threads < 32) threads = 32;
@@ -250,7 +251,7 @@ pthr_status one_emcs(pthr_batch *b) {
     }
     CUDA_TRY(b, launch_swap(b->dev, PTHR_SWAP_PT | (c->er_on ? PTHR_SWAP_ER : 0), 0, c->n_samples,
                             b->stream), "swap launch");
-    CUDA_TRY(b, launch_measure(b->dev, 0, c->n_samples, b->stream), "measure launch");
+    CUDA_TRY(b, launch_measure(b->dev, 0, c->n_samples, 0, b->stream), "measure launch");
     return PTHR_OK;
 }
 
@@ -326,6 +327,7 @@ PTHR_API pthr_status pthr_create_batch(const pthr_config *cfg, void *device_work
     d.active = (uint8_t *)(base + l.off[PTHR_BUF_ACTIVE]);
     d.status = (uint32_t *)(base + l.off[PTHR_BUF_STATUS]);
     d.cstat = (long long *)(base + l.off[PTHR_BUF_CSTAT]);
+    d.chaos = (double *)(base + l.off[PTHR_BUF_CHAOS]);
     d.S = cfg->n_samples;
     d.L = cfg->L;
     d.NT = cfg->n_temps;
@@ -406,7 +408,7 @@ PTHR_API pthr_status pthr_get_tuning(const pthr_batch *b, pthr_tuning *t) {
     t->pt_lattices_per_block = sh.K_pt;
     t->res_lattices_per_block = sh.K_res;
     t->sweep_threads = sh.threads;
-    t->cluster_threads = b->tuning.cluster_threads > 0 ? b->tuning.cluster_threads : 256;
+    t->cluster_threads = b->tuning.cluster_threads > 0 ? b->tuning.cluster_threads : 512;
     t->cluster_iter_cap = b->tuning.cluster_iter_cap;
     return PTHR_OK;
 }
@@ -451,15 +453,19 @@ PTHR_API pthr_status pthr_observables(pthr_batch *b, int flags, void *out, size_
     if ((flags & (PTHR_OBS_READ_HOST | PTHR_OBS_READ_DEVICE)) && (!out || bytes < need))
         return fail(b, PTHR_E_INVAL, "output buffer needs %zu bytes", need);
     if (flags & PTHR_OBS_MEASURE)
-        CUDA_TRY(b, launch_measure(b->dev, 0, b->cfg.n_samples, b->stream), "measure launch");
+        CUDA_TRY(b, launch_measure(b->dev, 0, b->cfg.n_samples, (flags & PTHR_OBS_CHAOS) ? 1 : 0,
+                                   b->stream), "measure launch");
     if (flags & PTHR_OBS_READ_DEVICE)
         CUDA_TRY(b, cudaMemcpyAsync(out, b->dev.obs, need, cudaMemcpyDeviceToDevice, b->stream), "obs copy");
     if (flags & PTHR_OBS_READ_HOST) {
         CUDA_TRY(b, cudaMemcpyAsync(out, b->dev.obs, need, cudaMemcpyDeviceToHost, b->stream), "obs copy");
         CUDA_TRY(b, cudaStreamSynchronize(b->stream), "obs sync");
     }
-    if (flags & PTHR_OBS_RESET)
+    if (flags & PTHR_OBS_RESET) {
         CUDA_TRY(b, cudaMemsetAsync(b->dev.obs, 0, need, b->stream), "obs reset");
+        CUDA_TRY(b, cudaMemsetAsync(b->dev.chaos, 0, (size_t)b->cfg.n_samples * b->cfg.n_temps * 2 * sizeof(double),
+                                    b->stream), "chaos reset");
+    }
     return PTHR_OK;
 }
 

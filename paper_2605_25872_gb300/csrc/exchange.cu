@@ -81,8 +81,34 @@ __global__ void swap_kernel(Batch b, int flags, int first) {
 // One block per (sample, temperature index k).  Accumulator layout per
 // (s, k): [0] measurements, [1] sum e, [2] sum e^2 (over groups), [3] sum q,
 // [4] sum q^2, [5] sum q_l, [6] sum S, [7] sum q^4 (over pairs).
+// Number of sites where two clones' overlaps q_i differ from a reference
+// pair: here, sites where clones A and B differ (for q) and links whose two
+// site overlaps differ (for q_l).
 template <int L>
-__global__ void measure_kernel(Batch b, int first) {
+__device__ __forceinline__ void overlap_counts(const unsigned char *A, const unsigned char *B, int tid,
+                                               int T, int &nneg, int &ndiff) {
+    constexpr int V = L * L * L;
+    nneg = 0;
+    ndiff = 0;
+    for (int i = tid; i < V; i += T) {
+        int w, by;
+        site_slot<L>(i, w, by);
+        const int qi = (A[4 * w + by] ^ B[4 * w + by]) >> 7;
+        nneg += qi;
+        const int x = i % L, y = (i / L) % L, z = i / (L * L);
+        const int nb[3] = {((x + 1) % L) + L * (y + L * z), x + L * (((y + 1) % L) + L * z),
+                           x + L * (y + L * ((z + 1) % L))};
+#pragma unroll
+        for (int mu = 0; mu < 3; ++mu) {
+            site_slot<L>(nb[mu], w, by);
+            const int qj = (A[4 * w + by] ^ B[4 * w + by]) >> 7;
+            ndiff += qi ^ qj;
+        }
+    }
+}
+
+template <int L>
+__global__ void measure_kernel(Batch b, int first, int chaos) {
     using Gm = Geom<L>;
     constexpr int V = Gm::V, LW = Gm::LAT_WORDS;
     const int s = first + blockIdx.x;
@@ -109,22 +135,8 @@ __global__ void measure_kernel(Batch b, int first) {
         const int lb = (2 * P + 1) * b.NSLOT + b.perm[((size_t)s * b.NR + 2 * P + 1) * b.NSLOT + k];
         const unsigned char *A = reinterpret_cast<const unsigned char *>(b.spins + ((size_t)s * b.NLAT + la) * LW);
         const unsigned char *B = reinterpret_cast<const unsigned char *>(b.spins + ((size_t)s * b.NLAT + lb) * LW);
-        int nneg = 0, ndiff = 0;
-        for (int i = tid; i < V; i += T) {
-            int w, by;
-            site_slot<L>(i, w, by);
-            const int qi = (A[4 * w + by] ^ B[4 * w + by]) >> 7;
-            nneg += qi;
-            const int x = i % L, y = (i / L) % L, z = i / (L * L);
-            const int nb[3] = {((x + 1) % L) + L * (y + L * z), x + L * (((y + 1) % L) + L * z),
-                               x + L * (y + L * ((z + 1) % L))};
-#pragma unroll
-            for (int mu = 0; mu < 3; ++mu) {
-                site_slot<L>(nb[mu], w, by);
-                const int qj = (A[4 * w + by] ^ B[4 * w + by]) >> 7;
-                ndiff += qi ^ qj;
-            }
-        }
+        int nneg, ndiff;
+        overlap_counts<L>(A, B, tid, T, nneg, ndiff);
         nneg = __reduce_add_sync(0xffffffffu, nneg);
         ndiff = __reduce_add_sync(0xffffffffu, ndiff);
         if ((tid & 31) == 0) { s_neg[tid >> 5] = nneg; s_diff[tid >> 5] = ndiff; }
@@ -144,6 +156,25 @@ __global__ void measure_kernel(Batch b, int first) {
             o[7] = __dadd_rn(o[7], __dmul_rn(__dmul_rn(q2, q), q));
         }
         __syncthreads();
+        if (chaos) {
+            // temperature chaos: clone of group 2P at T_0 against group 2P+1 at T_k
+            const int l0 = 2 * P * b.NSLOT + b.perm[((size_t)s * b.NR + 2 * P) * b.NSLOT + 0];
+            const unsigned char *A0 = reinterpret_cast<const unsigned char *>(b.spins + ((size_t)s * b.NLAT + l0) * LW);
+            int cneg, cdiff;
+            overlap_counts<L>(A0, B, tid, T, cneg, cdiff);
+            cneg = __reduce_add_sync(0xffffffffu, cneg);
+            if ((tid & 31) == 0) s_neg[tid >> 5] = cneg;
+            __syncthreads();
+            if (tid == 0) {
+                int tn = 0;
+                for (int w = 0; w < T / 32; ++w) tn += s_neg[w];
+                const double q = __ddiv_rn((double)(V - 2 * tn), (double)V);
+                double *c = b.chaos + ((size_t)s * b.NT + k) * 2;
+                c[0] = __dadd_rn(c[0], 1.0);
+                c[1] = __dadd_rn(c[1], __dmul_rn(q, q));
+            }
+            __syncthreads();
+        }
     }
 }
 
@@ -162,9 +193,9 @@ cudaError_t launch_swap(const Batch &b, int flags, int first, int count, cudaStr
     return cudaGetLastError();
 }
 
-cudaError_t launch_measure(const Batch &b, int first, int count, cudaStream_t st) {
+cudaError_t launch_measure(const Batch &b, int first, int count, int chaos, cudaStream_t st) {
     dim3 grid(count, b.NT);
-#define X(LL) if (b.L == LL) { measure_kernel<LL><<<grid, 256, 0, st>>>(b, first); return cudaGetLastError(); }
+#define X(LL) if (b.L == LL) { measure_kernel<LL><<<grid, 256, 0, st>>>(b, first, chaos); return cudaGetLastError(); }
     PTHR_FOR_EACH_L(X)
 #undef X
     return cudaErrorInvalidValue;

@@ -86,6 +86,7 @@ __global__ void init_meta_kernel(Batch b, int first, int count) {
     for (int i = threadIdx.x; i < b.NR; i += blockDim.x) b.trips[(size_t)s * b.NR + i] = 0;
     for (int i = threadIdx.x; i < b.NR * b.NT; i += blockDim.x) b.ptacc[(size_t)s * b.NR * b.NT + i] = 0;
     for (int i = threadIdx.x; i < b.NT * PTHR_NOBS; i += blockDim.x) b.obs[(size_t)s * b.NT * PTHR_NOBS + i] = 0.0;
+    for (int i = threadIdx.x; i < b.NT * 2; i += blockDim.x) b.chaos[(size_t)s * b.NT * 2 + i] = 0.0;
     const int ncs = (b.NPAIR > 0 ? b.NPAIR : 1) * b.NT * 4;
     for (int i = threadIdx.x; i < ncs; i += blockDim.x) b.cstat[(size_t)s * ncs + i] = 0;
     if (threadIdx.x == 0) {

@@ -36,7 +36,7 @@ size_t cluster_smem_bytes_for(int L);
 
 // exchange.cu
 cudaError_t launch_swap(const Batch &b, int flags, int first, int count, cudaStream_t st);
-cudaError_t launch_measure(const Batch &b, int first, int count, cudaStream_t st);
+cudaError_t launch_measure(const Batch &b, int first, int count, int chaos, cudaStream_t st);
 
 // init.cu
 cudaError_t launch_couplings_from_seed(const Batch &b, int first, int count, cudaStream_t st);

@@ -68,6 +68,7 @@ struct Batch {
     uint8_t *active;          // [S]
     uint32_t *status;         // [4]
     long long *cstat;         // [S][NPAIR][NT][4]
+    double *chaos;            // [S][NT][2]
     int S, L, NT, NR, NRES, NSLOT, NLAT, NPAIR, lat_words;
     int rule, cluster_mode, acu_interval, n_acu;
     double t_min, t_max;

@@ -448,3 +448,29 @@ def test_autotuner_returns_a_valid_faster_or_default_shape():
     a.emcs(3)
     b.emcs(3)
     _same(_state(a), _state(b))
+
+
+def test_chaos_accumulators_match_oracle():
+    """q^2 between the T_0 clone of group 2p and the T_k clone of group 2p+1,
+    accumulated on the GPU, equals the oracle's overlap of the same clones."""
+    cfg = BatchConfig(L=6, n_samples=2, n_temps=6, n_replicas=4, n_res=2, sweeps_per_emcs=1,
+                      res_sweeps_per_emcs=2)
+    gpu, mir = make(cfg, seed=21)
+    ref = np.zeros((cfg.n_samples, cfg.n_temps, 2))
+    for e in range(6):
+        gpu.sweep(1, 2)
+        gpu.houdayer()
+        gpu.swap(True, True)
+        gpu.measure(chaos=True)
+        mir.emcs()
+        if not np.array_equal(gpu_spins(gpu), mir.spins()):
+            pytest.skip("near tie changed the trajectory (rare)")
+        for s, smp in enumerate(mir.samples):
+            for k in range(cfg.n_temps):
+                for p in range(cfg.n_replicas // 2):
+                    ref[s, k, 0] += 1.0
+                    a = smp.spins[smp.lattice_at(2 * p, 0)]
+                    bb = smp.spins[smp.lattice_at(2 * p + 1, k)]
+                    q = O.pair_observables(cfg.L, smp.J, a, bb, 1.0)[0]
+                    ref[s, k, 1] += q * q
+    np.testing.assert_array_equal(gpu.chaos.cpu().numpy(), ref)
