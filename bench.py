@@ -217,7 +217,8 @@ def run_gpu(args):
 
     cfg = batch_config(args.samples)
     S = cfg.n_samples
-    seeds = W.sample_seeds(W.batch_seed(WL.index) + rank * S, S)
+    from paper_2605_25872_gb300.shard import shard_seeds
+    seeds = shard_seeds(W.batch_seed(WL.index), rank, world, world * S)   # global sample ids
     J = W.gaussian_couplings(WL.L, S, W.batch_seed(WL.index) + rank)
     stream = torch.cuda.Stream(dev)
     b = Batch(cfg, couplings=J, seeds=seeds, device=dev, stream=stream)
