@@ -64,7 +64,9 @@ def lib():
     global _lib
     with _lock:
         if _lib is None:
-            L = ctypes.CDLL(build())
+            # ORACLE_LIB: a prebuilt copy (the mutation tests load deliberately
+            # broken copies to show that the pins catch them)
+            L = ctypes.CDLL(os.environ.get("ORACLE_LIB") or build())
             vp, i, u32, u64, d = (ctypes.c_void_p, ctypes.c_int, ctypes.c_uint32,
                                   ctypes.c_uint64, ctypes.c_double)
             L.orc_philox4x32_10.argtypes = [vp, vp, vp]
