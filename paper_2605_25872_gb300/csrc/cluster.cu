@@ -55,8 +55,12 @@ __device__ __forceinline__ unsigned char spin_byte(const unsigned char *S, int i
     return S[4 * w + by];
 }
 
-template <int L>
-__global__ void __launch_bounds__(512) cluster_kernel(ClusterArgs a) {
+// CAPPED = false: every loop bound is the compile-time constant 4V+64 (the
+// production path; a runtime bound makes the labelling loops markedly
+// slower).  CAPPED = true: the bound comes from the tuning knob, used only to
+// exercise the error path.
+template <int L, bool CAPPED>
+__global__ void __launch_bounds__(1024) cluster_kernel(ClusterArgs a) {
     using Gm = Geom<L>;
     constexpr int V = Gm::V, LW = Gm::LAT_WORDS;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -106,7 +110,7 @@ __global__ void __launch_bounds__(512) cluster_kernel(ClusterArgs a) {
     }
     __syncthreads();
     bool ok = true;
-    const int cap = a.iter_cap > 0 ? a.iter_cap : 4 * V + 64;
+    const int cap = CAPPED ? a.iter_cap : 4 * V + 64;
     volatile int *vp = parent;
     for (int i = tid; i < V; i += T) {
         const unsigned char qi = flag[i];
@@ -266,13 +270,17 @@ template <int L>
 cudaError_t launch_cluster_L(const ClusterArgs &a, int threads, cudaStream_t st) {
     static bool configured = false;
     if (!configured) {
-        cudaError_t e = allow_max_dynamic_smem(cluster_kernel<L>);
+        cudaError_t e = allow_max_dynamic_smem(cluster_kernel<L, false>);
+        if (e == cudaSuccess) e = allow_max_dynamic_smem(cluster_kernel<L, true>);
         if (e != cudaSuccess) return e;
         configured = true;
     }
     const int blocks = a.sample_count * a.b.NPAIR * a.b.n_acu;
     if (blocks <= 0) return cudaSuccess;
-    cluster_kernel<L><<<blocks, threads, cluster_smem<L>(), st>>>(a);
+    if (a.iter_cap > 0)
+        cluster_kernel<L, true><<<blocks, threads, cluster_smem<L>(), st>>>(a);
+    else
+        cluster_kernel<L, false><<<blocks, threads, cluster_smem<L>(), st>>>(a);
     return cudaGetLastError();
 }
 
