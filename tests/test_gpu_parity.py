@@ -110,13 +110,14 @@ def test_init_state_matches_oracle(L):
 
 @pytest.mark.parametrize("L,rule", [(2, "metropolis"), (4, "metropolis"), (6, "metropolis"),
                                     (8, "metropolis"), (10, "metropolis"), (12, "metropolis"),
-                                    (14, "metropolis"), (16, "metropolis"), (8, "heatbath"),
-                                    (6, "heatbath")])
+                                    (14, "metropolis"), (16, "metropolis"), (18, "metropolis"),
+                                    (20, "metropolis"), (22, "metropolis"), (24, "metropolis"),
+                                    (8, "heatbath"), (6, "heatbath"), (18, "heatbath")])
 def test_sweep_trajectory_parity(L, rule):
     cfg = BatchConfig(L=L, n_samples=2, n_temps=6, n_replicas=2, n_res=2, rule=rule,
                       t_min=0.2, t_max=1.6)
     gpu, mir = make(cfg, seed=100 + L)
-    n = 60 if L >= 12 else 150
+    n = 150 if L < 12 else (60 if L <= 16 else 12)
     diverged, decisions = check_sweep_parity(gpu, mir, n)
     assert diverged <= max(1, TIE_RATE_MAX * decisions)
     if diverged == 0:
@@ -173,7 +174,7 @@ def test_offgrid_couplings_parity_with_fp32_error_margin():
 
 # ----------------------------------------------------------------------------- a5/a6
 
-@pytest.mark.parametrize("L", [2, 4, 6, 8, 10, 12, 16])
+@pytest.mark.parametrize("L", [2, 4, 6, 8, 10, 12, 16, 18, 24])
 def test_cluster_labels_bit_exact(L):
     cfg = BatchConfig(L=L, n_samples=2, n_temps=5, n_replicas=4, n_res=1)
     gpu, mir = make(cfg, seed=30 + L)
