@@ -350,7 +350,7 @@ def kernel_version():
     valid for the kernel it was measured on."""
     import hashlib
     h = hashlib.sha1()
-    for f in ("sweep_kernel.cuh", "sweep.cu", "sweep_table.h", "pthr_internal.cuh"):
+    for f in ("sweep_kernel.cuh", "geometry.cuh", "sweep.cu", "sweep_table.h", "pthr_internal.cuh"):
         with open(os.path.join(ROOT, "paper_2605_25872_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:12]

@@ -7,6 +7,7 @@
 // the clone that reached T_min, exchanges the clone at T_max with the oldest
 // reservoir clone, and finally the block advances the sample's EMCS counter.
 #include "kernels.cuh"
+#include "geometry.cuh"
 
 namespace pthr {
 
@@ -81,29 +82,32 @@ __global__ void swap_kernel(Batch b, int flags, int first) {
 // One block per (sample, temperature index k).  Accumulator layout per
 // (s, k): [0] measurements, [1] sum e, [2] sum e^2 (over groups), [3] sum q,
 // [4] sum q^2, [5] sum q_l, [6] sum S, [7] sum q^4 (over pairs).
-// Number of sites where two clones' overlaps q_i differ from a reference
-// pair: here, sites where clones A and B differ (for q) and links whose two
-// site overlaps differ (for q_l).
+// Overlap counts of clones A and B on the packed colour-row layout: nneg =
+// number of sites with q_i = -1, ndiff = number of forward links (i, i+mu)
+// with q_i != q_{i+mu}.  One 32-bit word holds four same-colour sites; the
+// XOR of the two clones' words has bit 7 of a byte set where q_i = -1, and
+// each word is compared with the words of its +x, +y, +z neighbours (the
+// same words the sweep reads).
 template <int L>
-__device__ __forceinline__ void overlap_counts(const unsigned char *A, const unsigned char *B, int tid,
+__device__ __forceinline__ void overlap_counts(const uint32_t *A, const uint32_t *B, int tid,
                                                int T, int &nneg, int &ndiff) {
-    constexpr int V = L * L * L;
+    using Gm = Geom<L>;
+    constexpr int W = Gm::W, ROWS = Gm::ROWS;
     nneg = 0;
     ndiff = 0;
-    for (int i = tid; i < V; i += T) {
-        int w, by;
-        site_slot<L>(i, w, by);
-        const int qi = (A[4 * w + by] ^ B[4 * w + by]) >> 7;
-        nneg += qi;
-        const int x = i % L, y = (i / L) % L, z = i / (L * L);
-        const int nb[3] = {((x + 1) % L) + L * (y + L * z), x + L * (((y + 1) % L) + L * z),
-                           x + L * (y + L * ((z + 1) % L))};
-#pragma unroll
-        for (int mu = 0; mu < 3; ++mu) {
-            site_slot<L>(nb[mu], w, by);
-            const int qj = (A[4 * w + by] ^ B[4 * w + by]) >> 7;
-            ndiff += qi ^ qj;
-        }
+    for (int w = tid; w < Gm::LAT_WORDS; w += T) {
+        const int c = w / (ROWS * W);
+        const int g = w - c * ROWS * W;
+        const GroupGeo q = group_geo<L>(g, c);
+        const uint32_t vm = valid_mask<L>(g % W);
+        const uint32_t qw = (A[q.own] ^ B[q.own]) & vm;
+        const uint32_t xa = A[q.xa] ^ B[q.xa];
+        const uint32_t xs = __byte_perm(A[q.wA] ^ B[q.wA], A[q.wB] ^ B[q.wB], q.selx);
+        const uint32_t qxp = q.par ? xs : xa;
+        const uint32_t qyp = A[q.yp] ^ B[q.yp];
+        const uint32_t qzp = A[q.zp] ^ B[q.zp];
+        nneg += __popc(qw);
+        ndiff += __popc((qw ^ qxp) & vm) + __popc((qw ^ qyp) & vm) + __popc((qw ^ qzp) & vm);
     }
 }
 
@@ -133,8 +137,8 @@ __global__ void measure_kernel(Batch b, int first, int chaos) {
     for (int P = 0; P < b.NPAIR; ++P) {
         const int la = 2 * P * b.NSLOT + b.perm[((size_t)s * b.NR + 2 * P) * b.NSLOT + k];
         const int lb = (2 * P + 1) * b.NSLOT + b.perm[((size_t)s * b.NR + 2 * P + 1) * b.NSLOT + k];
-        const unsigned char *A = reinterpret_cast<const unsigned char *>(b.spins + ((size_t)s * b.NLAT + la) * LW);
-        const unsigned char *B = reinterpret_cast<const unsigned char *>(b.spins + ((size_t)s * b.NLAT + lb) * LW);
+        const uint32_t *A = b.spins + ((size_t)s * b.NLAT + la) * LW;
+        const uint32_t *B = b.spins + ((size_t)s * b.NLAT + lb) * LW;
         int nneg, ndiff;
         overlap_counts<L>(A, B, tid, T, nneg, ndiff);
         nneg = __reduce_add_sync(0xffffffffu, nneg);
@@ -159,7 +163,7 @@ __global__ void measure_kernel(Batch b, int first, int chaos) {
         if (chaos) {
             // temperature chaos: clone of group 2P at T_0 against group 2P+1 at T_k
             const int l0 = 2 * P * b.NSLOT + b.perm[((size_t)s * b.NR + 2 * P) * b.NSLOT + 0];
-            const unsigned char *A0 = reinterpret_cast<const unsigned char *>(b.spins + ((size_t)s * b.NLAT + l0) * LW);
+            const uint32_t *A0 = b.spins + ((size_t)s * b.NLAT + l0) * LW;
             int cneg, cdiff;
             overlap_counts<L>(A0, B, tid, T, cneg, cdiff);
             cneg = __reduce_add_sync(0xffffffffu, cneg);
