@@ -2,15 +2,22 @@
 // update (ACU) and the original single-cluster Houdayer move, one block per
 // replica pair at one temperature.
 //
-// The block copies the two clones into shared memory, computes the site
-// overlaps q_i = s^a_i s^b_i (Eq. (2)), labels the connected components of
-// {i ~ j : neighbours, q_i = q_j} with a lock-free union-find in shared memory
-// (larger root always hooked under the smaller one, so every root is the
-// smallest site index of its cluster: the canonical label), draws one sign per
-// root from Philox keyed by that label, flips both clones, recomputes both
-// energies (FP64) and writes the pair back.  Every loop is bounded; hitting a
+// The block copies the two clones into shared memory and computes the site
+// overlaps q_i = s^a_i s^b_i (Eq. (2)) with one XOR per 4-site word.  It then
+// labels the connected components of {i ~ j : neighbours, q_i = q_j}:
+//  1. runs of equal q along each x row (with the periodic wrap) become stars
+//     rooted at their smallest site;
+//  2. a lock-free union-find in shared memory joins runs across y and z
+//     edges, always hooking the larger root under the smaller one, so every
+//     root is the smallest site index of its cluster (the canonical label).
+//     An edge whose left neighbours in both rows are in the same two runs is
+//     implied by that neighbouring edge and skipped; x = 0 never skips.
+// One sign per root is drawn from Philox keyed by the label; both clones flip
+// word by word, both energies are recomputed in FP64 (exact FP32 pairs per
+// thread) and the pair is written back.  Every loop is bounded; hitting a
 // bound sets STATUS_NOCONVERGE instead of spinning.
 #include "kernels.cuh"
+#include "geometry.cuh"
 
 namespace pthr {
 
@@ -40,19 +47,17 @@ __device__ __forceinline__ void unite(volatile int *parent, int a, int b, int ca
     ok = false;
 }
 
+// natural site index of byte kk of packed word w
 template <int L>
-__device__ __forceinline__ int neighbour(int i, int mu) {
-    const int x = i % L, y = (i / L) % L, z = i / (L * L);
-    if (mu == 0) return ((x + 1) % L) + L * (y + L * z);
-    if (mu == 1) return x + L * (((y + 1) % L) + L * z);
-    return x + L * (y + L * ((z + 1) % L));
-}
-
-template <int L>
-__device__ __forceinline__ unsigned char spin_byte(const unsigned char *S, int i) {
-    int w, by;
-    site_slot<L>(i, w, by);
-    return S[4 * w + by];
+__device__ __forceinline__ int site_of_word(int w, int kk) {
+    using Gm = Geom<L>;
+    constexpr int W = Gm::W, ROWS = Gm::ROWS;
+    const int c = w / (ROWS * W);
+    const int g = w - c * ROWS * W;
+    const int r = g / W, j = g - (g / W) * W;
+    const int y = r % L, z = r / L;
+    const int x = 2 * (4 * j + kk) + ((c + y + z) & 1);
+    return x + L * r;
 }
 
 // CAPPED = false: every loop bound is the compile-time constant 4V+64 (the
@@ -60,15 +65,15 @@ __device__ __forceinline__ unsigned char spin_byte(const unsigned char *S, int i
 // slower).  CAPPED = true: the bound comes from the tuning knob, used only to
 // exercise the error path.
 template <int L, bool CAPPED>
-__global__ void __launch_bounds__(1024) cluster_kernel(ClusterArgs a) {
+__global__ void __launch_bounds__(512, 4) cluster_kernel(ClusterArgs a) {
     using Gm = Geom<L>;
-    constexpr int V = Gm::V, LW = Gm::LAT_WORDS;
+    constexpr int V = Gm::V, LW = Gm::LAT_WORDS, W = Gm::W, Lh = Gm::Lh;
     extern __shared__ __align__(16) unsigned char smem[];
     int *parent = reinterpret_cast<int *>(smem);                       // [V]
     int *cnt = parent + V;                                             // [V]
     uint32_t *sa = reinterpret_cast<uint32_t *>(cnt + V);              // [LW]
     uint32_t *sb = sa + LW;                                            // [LW]
-    unsigned char *flag = reinterpret_cast<unsigned char *>(sb + LW);  // [V]
+    unsigned char *flag = reinterpret_cast<unsigned char *>(sb + LW);  // [V] q bit, later root flag
     __shared__ int s_ok;
     __shared__ int s_nneg, s_root, s_nclus, s_nflip;
     __shared__ int s_top[2][32];
@@ -100,25 +105,46 @@ __global__ void __launch_bounds__(1024) cluster_kernel(ClusterArgs a) {
         reinterpret_cast<uint4 *>(sb)[i] = reinterpret_cast<const uint4 *>(gb_ptr)[i];
     }
     __syncthreads();
-    const unsigned char *A = reinterpret_cast<const unsigned char *>(sa);
-    const unsigned char *B = reinterpret_cast<const unsigned char *>(sb);
-    // q_i < 0 <=> the two bytes differ (0x3F vs 0xBF)
-    for (int i = tid; i < V; i += T) {
-        flag[i] = (spin_byte<L>(A, i) ^ spin_byte<L>(B, i)) >> 7;
-        parent[i] = i;
-        cnt[i] = 0;
+    // q_i < 0 <=> the two bytes differ (0x3F vs 0xBF): one XOR per 4 sites
+    for (int w = tid; w < LW; w += T) {
+        const uint32_t qw = sa[w] ^ sb[w];
+        const int j = (w % (Gm::ROWS * W)) % W;
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+            if (!Gm::FULL && 4 * j + kk >= Lh) continue;
+            const int i = site_of_word<L>(w, kk);
+            flag[i] = (unsigned char)((qw >> (8 * kk + 7)) & 1u);
+            cnt[i] = 0;
+        }
     }
     __syncthreads();
+    // 1. runs of equal q along each periodic x row, rooted at their first site
+    for (int r = tid; r < L * L; r += T) {
+        const int i0 = L * r;
+        parent[i0] = i0;
+        for (int x = 1; x < L; ++x) {
+            const int i = i0 + x;
+            parent[i] = (flag[i] == flag[i - 1]) ? parent[i - 1] : i;
+        }
+        if (flag[i0 + L - 1] == flag[i0]) {     // the last run wraps onto the first
+            const int last = parent[i0 + L - 1];
+            if (last != i0)
+                for (int x = L - 1; x > 0 && parent[i0 + x] == last; --x) parent[i0 + x] = i0;
+        }
+    }
+    __syncthreads();
+    // 2. join runs across y and z edges
     bool ok = true;
     const int cap = CAPPED ? a.iter_cap : 4 * V + 64;
     volatile int *vp = parent;
     for (int i = tid; i < V; i += T) {
+        const int x = i % L, y = (i / L) % L, z = i / (L * L);
         const unsigned char qi = flag[i];
-#pragma unroll
-        for (int mu = 0; mu < 3; ++mu) {
-            const int j = neighbour<L>(i, mu);
-            if (flag[j] == qi) unite(vp, i, j, cap, ok);
-        }
+        const bool left_same = x != 0 && flag[i - 1] == qi;
+        const int jy = x + L * (((y + 1) % L) + L * z);
+        const int jz = x + L * (y + L * ((z + 1) % L));
+        if (flag[jy] == qi && !(left_same && flag[jy - 1] == qi)) unite(vp, i, jy, cap, ok);
+        if (flag[jz] == qi && !(left_same && flag[jz - 1] == qi)) unite(vp, i, jz, cap, ok);
     }
     __syncthreads();
     for (int i = tid; i < V; i += T) {
@@ -135,8 +161,13 @@ __global__ void __launch_bounds__(1024) cluster_kernel(ClusterArgs a) {
         int32_t *out = a.labels_out + ((size_t)(s * b.NPAIR + P) * b.NT + k) * V;
         for (int i = tid; i < V; i += T) out[i] = parent[i];
     }
-    // cluster sizes (statistics)
-    for (int i = tid; i < V; i += T) atomicAdd(&cnt[parent[i]], 1);
+    // cluster sizes (statistics): one atomic per distinct root per warp
+    for (int i0 = 0; i0 < V; i0 += T) {
+        const int i = i0 + tid;
+        const int root = i < V ? parent[i] : -1;
+        const unsigned peers = __match_any_sync(0xffffffffu, root);
+        if (i < V && (tid & 31) == __ffs(peers) - 1) atomicAdd(&cnt[root], __popc(peers));
+    }
     __syncthreads();
     if (a.label_only) return;
 
@@ -184,18 +215,20 @@ __global__ void __launch_bounds__(1024) cluster_kernel(ClusterArgs a) {
             if (parent[i] == i) flag[i] = (unsigned char)(i == root);
         __syncthreads();
     }
-    // flip both clones on the selected clusters
-    unsigned char *Aw = reinterpret_cast<unsigned char *>(sa);
-    unsigned char *Bw = reinterpret_cast<unsigned char *>(sb);
+    // flip both clones on the selected clusters, one 4-site word at a time
     int nflip = 0;
-    for (int i = tid; i < V; i += T) {
-        if (flag[parent[i]]) {
-            int w, by;
-            site_slot<L>(i, w, by);
-            Aw[4 * w + by] ^= 0x80u;
-            Bw[4 * w + by] ^= 0x80u;
-            ++nflip;
+    for (int w = tid; w < LW; w += T) {
+        const int j = (w % (Gm::ROWS * W)) % W;
+        uint32_t m = 0u;
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+            if (!Gm::FULL && 4 * j + kk >= Lh) continue;
+            const int i = site_of_word<L>(w, kk);
+            if (flag[parent[i]]) m |= 0x80u << (8 * kk);
         }
+        sa[w] ^= m;
+        sb[w] ^= m;
+        nflip += __popc(m);
     }
     // statistics: number of clusters, two largest sizes
     int nroots = 0, t1 = 0, t2 = 0;
@@ -208,7 +241,6 @@ __global__ void __launch_bounds__(1024) cluster_kernel(ClusterArgs a) {
     }
     atomicAdd(&s_nclus, nroots);
     atomicAdd(&s_nflip, nflip);
-    // warp top-2 then block top-2
     for (int o = 16; o > 0; o >>= 1) {
         const int u1 = __shfl_xor_sync(0xffffffffu, t1, o), u2 = __shfl_xor_sync(0xffffffffu, t2, o);
         int n1, n2;
@@ -217,20 +249,33 @@ __global__ void __launch_bounds__(1024) cluster_kernel(ClusterArgs a) {
     }
     if ((tid & 31) == 0) { s_top[0][tid >> 5] = t1; s_top[1][tid >> 5] = t2; }
     __syncthreads();
-    // energies of both clones (Eq. (1)), exact FP32 pairs then FP64
+    // energies of both clones (Eq. (1)) over the forward bonds of every
+    // 4-site word, exact FP32 pairs per thread then FP64
     const float *J = b.J + (size_t)s * 3 * V;
     float ha = 0.f, la_ = 0.f, hb = 0.f, lb_ = 0.f;
-    for (int i = tid; i < V; i += T) {
-        const float ai = spin_byte<L>(Aw, i) == SPIN_DN ? -1.f : 1.f;
-        const float bi = spin_byte<L>(Bw, i) == SPIN_DN ? -1.f : 1.f;
+    for (int w = tid; w < LW; w += T) {
+        const int c = w / (Gm::ROWS * W);
+        const int g = w - c * Gm::ROWS * W;
+        const GroupGeo q = group_geo<L>(g, c);
+        const int j = g % W;
+        const uint32_t X = 0x3F3F3F3Fu;
+        const uint32_t oA = sa[q.own], oB = sb[q.own];
+        const uint32_t xA = q.par ? __byte_perm(sa[q.wA], sa[q.wB], q.selx) : sa[q.xa];
+        const uint32_t xB = q.par ? __byte_perm(sb[q.wA], sb[q.wB], q.selx) : sb[q.xa];
+        // bytes 0x3F where s_i s_{i+mu} = +1, 0xBF where -1
+        const uint32_t pxA = oA ^ xA ^ X, pyA = oA ^ sa[q.yp] ^ X, pzA = oA ^ sa[q.zp] ^ X;
+        const uint32_t pxB = oB ^ xB ^ X, pyB = oB ^ sb[q.yp] ^ X, pzB = oB ^ sb[q.zp] ^ X;
 #pragma unroll
-        for (int mu = 0; mu < 3; ++mu) {
-            const int j = neighbour<L>(i, mu);
-            const float Jm = J[mu * V + i];
-            const float aj = spin_byte<L>(Aw, j) == SPIN_DN ? -1.f : 1.f;
-            const float bj = spin_byte<L>(Bw, j) == SPIN_DN ? -1.f : 1.f;
-            two_sum_acc(ha, la_, ai * (Jm * aj));
-            two_sum_acc(hb, lb_, bi * (Jm * bj));
+        for (int kk = 0; kk < 4; ++kk) {
+            if (!Gm::FULL && 4 * j + kk >= Lh) continue;
+            const int i = site_of_word<L>(w, kk);
+            const float Jx = J[i], Jy = J[V + i], Jz = J[2 * V + i];
+            two_sum_acc(ha, la_, Jx * spinf(pxA, kk));
+            two_sum_acc(ha, la_, Jy * spinf(pyA, kk));
+            two_sum_acc(ha, la_, Jz * spinf(pzA, kk));
+            two_sum_acc(hb, lb_, Jx * spinf(pxB, kk));
+            two_sum_acc(hb, lb_, Jy * spinf(pyB, kk));
+            two_sum_acc(hb, lb_, Jz * spinf(pzB, kk));
         }
     }
     double ea = (double)ha + (double)la_, eb = (double)hb + (double)lb_;
