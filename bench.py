@@ -433,7 +433,7 @@ def run_serve(args):
         slots = int(min(args.serve_max_slots, (mem / len(W.SERVE_SIZES)) // one))
         specs.append(PoolSpec(L=L, slots=slots, n_temps=24))
     # capacity probe: every pool full, EMCS steps timed with all pools in flight
-    srv = Server(specs)
+    srv = Server(specs, use_group=args.serve_group)
     probe = [Request(rid=-1 - i * 100000 - k, L=sp.L, seed=10 ** 6 + i * 100000 + k, budget_emcs=10 ** 6)
              for i, sp in enumerate(specs) for k in range(sp.slots)]
     per_emcs_s = srv.fill_and_time(probe, 5)
@@ -445,7 +445,7 @@ def run_serve(args):
     times, Ls = W.poisson_arrivals(n_req, lam, W.batch_seed(5))
     reqs = [Request(rid=i, L=int(Ls[i]), seed=W.batch_seed(5) + 7919 * i, budget_emcs=budget,
                     arrival=float(times[i])) for i in range(n_req)]
-    srv = Server(specs)
+    srv = Server(specs, use_group=args.serve_group)
     srv.run(reqs, realtime=True)
     st = srv.stats()
     line = {"mode": "serve", "metric": "time-to-budget p50/p99 and aggregate spin updates/ns",
@@ -453,6 +453,7 @@ def run_serve(args):
             "requests": st["requests"], "budget_emcs": budget, "lambda_per_s": lam,
             "capacity_per_s": cap, "full_pool_emcs_s": per_emcs_s, "slots": {sp.L: sp.slots for sp in specs},
             "memory_budget_gb": args.serve_mem_gb, "emcs_steps": st["emcs_steps"],
+            "group_graph": bool(args.serve_group),
             "config": {"workload": "serving: L uniform in {6,8,10,12,16}, 24 T 0.2..1.6, 4 replicas + "
                                    "4 reservoir clones, paper EMCS, couplings drawn on the device from each "
                                    "request's seed, 960-sweep reservoir pre-thermalisation at admission"}}
@@ -462,11 +463,12 @@ def run_serve(args):
 
 def run_autotune(args):
     from paper_2605_25872_gb300.build import build
-    from paper_2605_25872_gb300.autotune import autotune
+    from paper_2605_25872_gb300.autotune import autotune, autotune_schedule
     build()
     cfg = batch_config(args.samples)
     shape = autotune(cfg, emcs=3, use_cache=False, verbose=True)
-    print(json.dumps({"mode": "autotune", "best": shape}))
+    k, table = autotune_schedule(cfg)
+    print(json.dumps({"mode": "autotune", "best_shape": shape, "acu_interval": k, "schedule": table}))
     return 0
 
 
@@ -485,6 +487,9 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=200)
     ap.add_argument("--serve-mem-gb", type=float, default=2.0)
     ap.add_argument("--serve-max-slots", type=int, default=128)
+    ap.add_argument("--serve-group", action="store_true",
+                    help="advance all pools with one group graph per EMCS (admissions then "
+                         "delay every pool, so per-pool stepping is the default)")
     ap.add_argument("--autotune", action="store_true", help="print the shape sweep for the workload")
     args = ap.parse_args()
     if args.serve:

@@ -249,6 +249,19 @@ PTHR_API pthr_status pthr_reset_samples(pthr_batch *b, int first, int count,
 /* Mark samples [first, first+count) active (1) or idle (0). */
 PTHR_API pthr_status pthr_set_active(pthr_batch *b, int first, int count, int active);
 
+/* Groups: several batches (for instance one per lattice size) advanced
+ * together.  pthr_group_create captures one EMCS of every batch -- each on
+ * its own stream, forked from and joined to `stream` -- into one CUDA graph;
+ * pthr_group_emcs replays it n times on `stream`, so mixed-L work runs as one
+ * launch per EMCS with the batches overlapping on the device.  The batches
+ * must be at an EMCS boundary, must not be destroyed before the group, and
+ * their idle slots cost no work.  Kernel shapes are fixed at creation. */
+typedef struct pthr_group pthr_group;
+PTHR_API pthr_status pthr_group_create(pthr_batch *const *batches, int n, void *stream,
+                                       pthr_group **out);
+PTHR_API pthr_status pthr_group_emcs(pthr_group *g, int n);
+PTHR_API void pthr_group_destroy(pthr_group *g);
+
 /* Checkpoint: the workspace holds the whole state (counter-based random
  * numbers make resume exact), so a blob is the workspace plus a header.
  * pthr_save with blob == NULL returns the size in *bytes; otherwise blob

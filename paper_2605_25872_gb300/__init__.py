@@ -6,6 +6,6 @@ The compute lives in libpthr.so (CUDA kernels behind the C ABI of
 include/pthr.h); this package only binds it.
 """
 from . import _lib  # noqa: F401
-from .batch import Batch, BatchConfig, required_bytes, buffer_info  # noqa: F401
+from .batch import Batch, BatchConfig, Group, required_bytes, buffer_info  # noqa: F401
 
-__all__ = ["Batch", "BatchConfig", "required_bytes", "buffer_info"]
+__all__ = ["Batch", "BatchConfig", "Group", "required_bytes", "buffer_info"]

@@ -30,7 +30,7 @@ EXPORTS = ("pthr_required_bytes", "pthr_buffer_info", "pthr_lattice_bytes", "pth
            "pthr_houdayer", "pthr_cluster_labels", "pthr_swap", "pthr_observables", "pthr_emcs",
            "pthr_prethermalize_reservoir", "pthr_poll", "pthr_export_spins", "pthr_import_spins",
            "pthr_reset_samples", "pthr_set_active", "pthr_save", "pthr_load", "pthr_last_error",
-           "pthr_version")
+           "pthr_version", "pthr_group_create", "pthr_group_emcs", "pthr_group_destroy")
 
 
 class Config(ctypes.Structure):
@@ -91,6 +91,8 @@ def load(path: str = LIB_PATH):
         "pthr_set_active": [vp, i, i, i],
         "pthr_save": [vp, vp, P(sz)],
         "pthr_load": [vp, vp, sz],
+        "pthr_group_create": [vp, i, vp, P(vp)],
+        "pthr_group_emcs": [vp, i],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -98,6 +100,8 @@ def load(path: str = LIB_PATH):
         f.restype = ctypes.c_int
     L.pthr_destroy.argtypes = [vp]
     L.pthr_destroy.restype = None
+    L.pthr_group_destroy.argtypes = [vp]
+    L.pthr_group_destroy.restype = None
     L.pthr_last_error.argtypes = [vp]
     L.pthr_last_error.restype = ctypes.c_char_p
     L.pthr_version.argtypes = []

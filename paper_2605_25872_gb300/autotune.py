@@ -110,3 +110,55 @@ def tuned_batch(cfg: BatchConfig, **kw) -> Batch:
     if shape:
         b.set_tuning(**shape)
     return b
+
+
+def autotune_schedule(cfg: BatchConfig, intervals=(1, 2, 4, 8), max_cluster_share: float = 0.10,
+                      emcs: int = 8, warm_emcs: int = 8, device="cuda"):
+    """Cluster-move schedule by cost balance.
+
+    The paper fixes its EMCS (10 local sweeps per cluster move, PT and ER
+    step) from a balance between the costs of the steps (Sec. 3).  Here the
+    interval between cluster moves (acu_interval, in EMCS) is chosen the same
+    way on this GPU: every candidate is timed on a warmed scratch batch (CUDA
+    events around the sweep and the cluster launches of each EMCS), and the
+    smallest interval whose cluster step takes at most max_cluster_share of
+    the EMCS time is returned with the measured table.  The interval changes
+    the Markov chain, not only its speed, so it is a recommendation that the
+    caller applies through BatchConfig.acu_interval.
+    """
+    import torch
+    rng = np.random.default_rng(1)
+    J = (np.rint(rng.standard_normal((cfg.n_samples, 3, cfg.L ** 3)) * 2 ** 18) / 2 ** 18).astype(np.float32)
+    table = []
+    for k in intervals:
+        c = BatchConfig(**{**cfg.__dict__, "acu_interval": int(k)})
+        st = torch.cuda.Stream(device)
+        b = Batch(c, couplings=J, device=device, stream=st)
+        if c.er_on and c.n_res:
+            b.prethermalize(960)
+        b.emcs(warm_emcs)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        sw = cl = tot = 0.0
+        with torch.cuda.stream(st):
+            for _ in range(emcs):
+                ev[0].record(st)
+                b.sweep(c.sweeps_per_emcs, c.res_sweeps_per_emcs if c.er_on else 0)
+                ev[1].record(st)
+                b.houdayer()
+                ev[2].record(st)
+                b.swap(True, c.er_on)
+                b.measure()
+                ev[3].record(st)
+                st.synchronize()
+                sw += ev[0].elapsed_time(ev[1])
+                cl += ev[1].elapsed_time(ev[2])
+                tot += ev[0].elapsed_time(ev[3])
+        table.append({"acu_interval": int(k), "ms_per_emcs": tot / emcs, "cluster_ms_per_emcs": cl / emcs,
+                      "sweep_ms_per_emcs": sw / emcs, "cluster_share": cl / tot})
+        b.close()
+    chosen = intervals[-1]
+    for row in table:
+        if row["cluster_share"] <= max_cluster_share:
+            chosen = row["acu_interval"]
+            break
+    return chosen, table

@@ -289,3 +289,36 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+class Group:
+    """Several batches (e.g. one per lattice size) advanced by one CUDA-graph
+    launch per EMCS; each batch runs on its own stream inside the graph."""
+
+    def __init__(self, batches, stream=None):
+        import torch
+        self.lib = _lib.load()
+        self.batches = list(batches)
+        self.stream = stream if stream is not None else torch.cuda.Stream(self.batches[0].device)
+        arr = (ctypes.c_void_p * len(self.batches))(*[b.h.value for b in self.batches])
+        h = ctypes.c_void_p()
+        check(self.lib.pthr_group_create(arr, len(self.batches), ctypes.c_void_p(self.stream.cuda_stream),
+                                         ctypes.byref(h)))
+        self.h = h
+
+    def emcs(self, n: int = 1):
+        check(self.lib.pthr_group_emcs(self.h, n))
+
+    def synchronize(self):
+        self.stream.synchronize()
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.pthr_group_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -626,6 +626,79 @@ PTHR_API pthr_status pthr_load(pthr_batch *b, const void *blob, size_t bytes) {
     return PTHR_OK;
 }
 
+struct pthr_group {
+    cudaStream_t stream;
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
+    int n;
+};
+
+PTHR_API pthr_status pthr_group_create(pthr_batch *const *batches, int n, void *stream, pthr_group **out) {
+    if (!batches || n < 1 || !out || !stream)
+        return fail(nullptr, PTHR_E_INVAL, "group needs batches, n >= 1, a non-default stream and out");
+    *out = nullptr;
+    for (int i = 0; i < n; ++i) {
+        if (!batches[i]) return fail(nullptr, PTHR_E_INVAL, "NULL batch in group");
+        if (batches[i]->pt_sweep_off || batches[i]->res_sweep_off)
+            return fail(nullptr, PTHR_E_STATE, "group batches must be at an EMCS boundary");
+        if (batches[i]->stream == nullptr || batches[i]->stream == (cudaStream_t)stream)
+            return fail(nullptr, PTHR_E_INVAL, "each batch needs its own non-default stream");
+    }
+    cudaStream_t master = (cudaStream_t)stream;
+    if (capturing(master)) return fail(nullptr, PTHR_E_STATE, "stream is already capturing");
+    cudaEvent_t fork = nullptr;
+    cudaEvent_t *join = new cudaEvent_t[n]();
+    cudaError_t e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+    for (int i = 0; i < n && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&join[i], cudaEventDisableTiming);
+    pthr_status st = PTHR_OK;
+    cudaGraph_t g = nullptr;
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(master, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        e = cudaEventRecord(fork, master);
+        for (int i = 0; i < n && e == cudaSuccess && st == PTHR_OK; ++i) {
+            e = cudaStreamWaitEvent(batches[i]->stream, fork, 0);
+            if (e == cudaSuccess) st = one_emcs(batches[i]);
+            if (e == cudaSuccess && st == PTHR_OK) e = cudaEventRecord(join[i], batches[i]->stream);
+            if (e == cudaSuccess && st == PTHR_OK) e = cudaStreamWaitEvent(master, join[i], 0);
+        }
+        cudaError_t e2 = cudaStreamEndCapture(master, &g);
+        if (e == cudaSuccess) e = e2;
+    }
+    cudaGraphExec_t exec = nullptr;
+    if (e == cudaSuccess && st == PTHR_OK) e = cudaGraphInstantiate(&exec, g, 0);
+    if (fork) cudaEventDestroy(fork);
+    for (int i = 0; i < n; ++i) if (join[i]) cudaEventDestroy(join[i]);
+    delete[] join;
+    if (st != PTHR_OK || e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        if (st != PTHR_OK) return fail(nullptr, st, "%s", batches[0]->err);
+        return cuda_fail(nullptr, e, "group capture");
+    }
+    pthr_group *grp = new pthr_group();
+    grp->stream = master;
+    grp->graph = g;
+    grp->exec = exec;
+    grp->n = n;
+    *out = grp;
+    return PTHR_OK;
+}
+
+PTHR_API pthr_status pthr_group_emcs(pthr_group *g, int n) {
+    if (!g || n < 0) return fail(nullptr, PTHR_E_INVAL, "bad group or count");
+    for (int i = 0; i < n; ++i) {
+        cudaError_t e = cudaGraphLaunch(g->exec, g->stream);
+        if (e != cudaSuccess) return cuda_fail(nullptr, e, "group graph launch");
+    }
+    return PTHR_OK;
+}
+
+PTHR_API void pthr_group_destroy(pthr_group *g) {
+    if (!g) return;
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    if (g->graph) cudaGraphDestroy(g->graph);
+    delete g;
+}
+
 PTHR_API const char *pthr_last_error(const pthr_batch *b) { return b ? b->err : g_err; }
 
 }  // extern "C"

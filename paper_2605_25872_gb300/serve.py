@@ -122,11 +122,16 @@ class GpuPool:
 
 
 class Server:
-    """Admission queue -> slots -> EMCS steps -> completion -> readback."""
+    """Admission queue -> slots -> EMCS steps -> completion -> readback.
 
-    def __init__(self, specs, pool_factory=None, clock=None):
+    With use_group=True (GPU pools) all pools advance by one CUDA-graph launch
+    per EMCS (pthr_group), each pool on its own stream inside the graph."""
+
+    def __init__(self, specs, pool_factory=None, clock=None, use_group=False):
         self.specs = {s.L: s for s in specs}
         self.pool_factory = pool_factory or (lambda spec: GpuPool(spec))
+        self.use_group = use_group
+        self.group = None
         self.pools = {L: self.pool_factory(s) for L, s in self.specs.items()}
         self.slot_req = {L: [None] * s.slots for L, s in self.specs.items()}
         self.remaining = {L: np.zeros(s.slots, dtype=np.int64) for L, s in self.specs.items()}
@@ -184,9 +189,20 @@ class Server:
 
     def _step_all(self):
         stepped = [L for L, sl in self.slot_req.items() if any(r is not None for r in sl)]
-        for L in stepped:                 # enqueue one EMCS per busy pool (streams overlap)
-            self.pools[L].step()
-            self.emcs_steps[L] += 1
+        if self.use_group:
+            from .batch import Group
+            if self.group is None:
+                self.group = Group([p.batch for p in self.pools.values()])
+            for p in self.pools.values():          # admissions on the pool streams first
+                self.group.stream.wait_stream(p.stream)
+            self.group.emcs(1)                     # every pool, one graph launch
+            self.group.synchronize()
+            for L in stepped:
+                self.emcs_steps[L] += 1
+        else:
+            for L in stepped:                 # enqueue one EMCS per busy pool (streams overlap)
+                self.pools[L].step()
+                self.emcs_steps[L] += 1
         for L in stepped:
             self.pools[L].wait()
             rem = self.remaining[L]

@@ -475,3 +475,13 @@ def test_chaos_accumulators_match_oracle():
                     q = O.pair_observables(cfg.L, smp.J, a, bb, 1.0)[0]
                     ref[s, k, 1] += q * q
     np.testing.assert_array_equal(gpu.chaos.cpu().numpy(), ref)
+
+
+def test_schedule_autotuner_reports_cluster_share():
+    from paper_2605_25872_gb300.autotune import autotune_schedule
+    cfg = BatchConfig(L=8, n_samples=8, n_temps=8, n_replicas=4, n_res=2, sweeps_per_emcs=2,
+                      res_sweeps_per_emcs=4)
+    k, table = autotune_schedule(cfg, intervals=(1, 4), emcs=4, warm_emcs=2)
+    assert k in (1, 4) and len(table) == 2
+    assert all(0.0 <= r["cluster_share"] < 1.0 for r in table)
+    assert table[1]["cluster_ms_per_emcs"] < table[0]["cluster_ms_per_emcs"]

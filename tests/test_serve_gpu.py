@@ -33,12 +33,13 @@ def alone(spec, req):
     return b.obs[0].cpu().numpy(), b.round_trips[0].cpu().numpy()
 
 
-def test_serving_result_alone_equals_in_the_mix():
+@pytest.mark.parametrize("use_group", [False, True])
+def test_serving_result_alone_equals_in_the_mix(use_group):
     specs = [PoolSpec(L=6, slots=3, n_temps=8, sweeps_per_emcs=2, res_sweeps_per_emcs=6,
                       pretherm_sweeps=12),
              PoolSpec(L=8, slots=2, n_temps=8, sweeps_per_emcs=2, res_sweeps_per_emcs=6,
                       pretherm_sweeps=12)]
-    srv = Server(specs)
+    srv = Server(specs, use_group=use_group)
     rng = np.random.default_rng(5)
     reqs = []
     for i in range(10):
@@ -55,3 +56,24 @@ def test_serving_result_alone_equals_in_the_mix():
         np.testing.assert_array_equal(r.round_trips, trips)
     st = srv.stats()
     assert st["p50_s"] > 0 and st["updates_per_ns"] > 0
+
+
+def test_group_graph_equals_separate_batches():
+    """pthr_group: one graph launch per EMCS over batches of different L gives
+    the same state as advancing each batch on its own."""
+    from paper_2605_25872_gb300 import Group
+    cfgs = [BatchConfig(L=L, n_samples=3, n_temps=6, n_replicas=4, n_res=2, sweeps_per_emcs=2,
+                        res_sweeps_per_emcs=4) for L in (6, 8, 12)]
+    Js = [W.gaussian_couplings(c.L, 3, 40 + c.L) for c in cfgs]
+    seeds = [W.sample_seeds(70 + c.L, 3) for c in cfgs]
+    sep = [Batch(c, couplings=J, seeds=sd) for c, J, sd in zip(cfgs, Js, seeds)]
+    grp_b = [Batch(c, couplings=J, seeds=sd, stream=torch.cuda.Stream()) for c, J, sd in zip(cfgs, Js, seeds)]
+    for b in sep:
+        b.emcs(5)
+    g = Group(grp_b)
+    g.emcs(5)
+    g.synchronize()
+    for a, b in zip(sep, grp_b):
+        np.testing.assert_array_equal(a.export_spins().cpu().numpy(), b.export_spins().cpu().numpy())
+        np.testing.assert_array_equal(a.obs.cpu().numpy(), b.obs.cpu().numpy())
+        np.testing.assert_array_equal(a.energies.cpu().numpy(), b.energies.cpu().numpy())
