@@ -1,0 +1,73 @@
+"""The plain L=4 workload over its whole budget: 2e4 EMCS (1 local sweep +
+ACU + PT + ER with 240 reservoir sweeps each), GPU against the FP64 oracle
+(C, whole EMCS), compared every 1000 EMCS.  A difference at a checkpoint
+(state or accumulators) is allowed only if the oracle counted a near tie in
+that interval; the GPU is then resynchronised from the oracle.  (Two
+Metropolis chains driven by the same random numbers can coalesce again after
+a near tie split them, so matching spins at a checkpoint do not imply
+matching accumulators.)"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+P = pytest.importorskip("paper_2605_25872_gb300")
+from paper_2605_25872_gb300 import Batch, BatchConfig  # noqa: E402
+from paper_2605_25872_gb300.build import build  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    build()
+
+
+def test_plain_L4_full_budget_2e4_emcs():
+    wl = W.WORKLOADS["c1"]
+    cfg = BatchConfig(L=wl.L, n_samples=1, n_temps=wl.n_temps, t_min=wl.t_min, t_max=wl.t_max,
+                      n_replicas=wl.n_replicas, n_res=wl.n_res, sweeps_per_emcs=wl.sweeps_per_emcs,
+                      res_sweeps_per_emcs=wl.res_sweeps_per_emcs)
+    J = W.gaussian_couplings(wl.L, 1, W.batch_seed(wl.index))
+    seed = W.batch_seed(wl.index)
+    gpu = Batch(cfg, couplings=J, seeds=[seed])
+    ref = O.OracleSample(wl.L, wl.n_temps, wl.t_min, wl.t_max, seed, J=J[0].astype(np.float64),
+                         n_groups=wl.n_replicas, n_res=wl.n_res, sweeps_per_emcs=wl.sweeps_per_emcs,
+                         res_sweeps_per_emcs=wl.res_sweeps_per_emcs)
+    total, chunk = wl.budget_emcs, 500
+    resyncs = 0
+    for done in range(0, total, chunk):
+        ties_before = int(ref.n_ties.sum())
+        gpu.emcs(chunk, graph=False)
+        ref.emcs(chunk)
+        g = gpu.export_spins().cpu().numpy()[0]
+        same = (np.array_equal(g, ref.spins) and np.array_equal(gpu.perm.cpu().numpy()[0].ravel(), ref.perm)
+                and np.array_equal(gpu.energies.cpu().numpy()[0], ref.E_lat)
+                and np.array_equal(gpu.obs.cpu().numpy()[0], ref.obs)
+                and np.array_equal(gpu.round_trips.cpu().numpy()[0], ref.round_trips))
+        if not same:
+            assert int(ref.n_ties.sum()) > ties_before, f"divergence without a near tie before EMCS {done + chunk}"
+            resyncs += 1
+            gpu.perm.copy_(torch.from_numpy(ref.perm.reshape(1, cfg.n_replicas, -1).astype(np.int32)))
+            gpu.age.copy_(torch.from_numpy(ref.age.reshape(1, cfg.n_replicas, -1).astype(np.int32)))
+            gpu.rt_state.copy_(torch.from_numpy(ref.rt_state[None]))
+            gpu.round_trips.copy_(torch.from_numpy(ref.round_trips[None]))
+            gpu.pt_accepted.copy_(torch.from_numpy(ref.pt_accepted.reshape(1, cfg.n_replicas, -1)))
+            gpu.obs.copy_(torch.from_numpy(ref.obs[None]))
+            gpu.import_spins(torch.from_numpy(ref.spins[None]))
+    decisions = total * (cfg.n_replicas * (wl.n_temps * wl.sweeps_per_emcs + wl.n_res * wl.res_sweeps_per_emcs)) * wl.L ** 3
+    n_int = total // chunk
+    # every divergent interval contained counted near ties (asserted above); the
+    # near-tie rate is the benchmark spec's < 1e-5 of decisions, and actual decision
+    # flips (at most one per divergent interval) are far rarer than near ties
+    assert ref.n_ties.sum() < 1e-5 * decisions
+    assert resyncs < n_int
+    assert resyncs <= 1e-3 * ref.n_ties.sum()
+    assert ref.round_trips.sum() > 0 and ref.pt_accepted.sum() > 0
+    print(f"c1 full budget: {total} EMCS, {decisions:.3g} local decisions, near ties "
+          f"{int(ref.n_ties.sum())} ({ref.n_ties.sum() / decisions:.2e}), divergent intervals "
+          f"{resyncs}/{n_int}, round trips {int(ref.round_trips.sum())}")
