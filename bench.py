@@ -36,7 +36,7 @@ import workloads as W  # noqa: E402
 
 METRIC = "spin updates/ns and PTHR sweeps/s at L=16 (FP32 batched vs plain)"
 UNIT = "spin-updates/ns"
-WL = W.WORKLOADS["c4"]
+WL = W.WORKLOADS["c4"]      # the headline workload; --workload selects another for reports
 # Algorithmic ALU work of one Metropolis spin update: a
 # quarter of a Philox4x32-10 call (10 rounds x (4 multiply halves + 2
 # three-input XORs) / 4 = 15), the 24-bit uniform (2), the local field
@@ -114,15 +114,15 @@ class ClockSampler:
 def batch_config(n_samples=None):
     from paper_2605_25872_gb300 import BatchConfig
     return BatchConfig(L=WL.L, n_samples=n_samples or WL.n_samples, n_temps=WL.n_temps,
-                       t_min=WL.t_min, t_max=WL.t_max, n_replicas=WL.n_replicas, n_res=WL.n_res,
-                       sweeps_per_emcs=WL.sweeps_per_emcs,
+                       t_min=WL.t_min, t_max=WL.t_max, n_replicas=WL.n_replicas,
+                       n_res=WL.n_res if WL.er_on else 0, sweeps_per_emcs=WL.sweeps_per_emcs,
                        res_sweeps_per_emcs=WL.res_sweeps_per_emcs, er_on=WL.er_on, cluster="acu")
 
 
 def updates_per_emcs(n_samples):
     V = WL.V
     pt = n_samples * WL.n_replicas * WL.n_temps * WL.sweeps_per_emcs * V
-    res = n_samples * WL.n_replicas * WL.n_res * WL.res_sweeps_per_emcs * V
+    res = n_samples * WL.n_replicas * WL.n_res * WL.res_sweeps_per_emcs * V if WL.er_on else 0
     return pt, res
 
 
@@ -139,7 +139,8 @@ def oracle_sample_run(n_threads, n_emcs=1, seed_offset=0):
     import oracle as O
     J = W.gaussian_couplings(WL.L, n_threads, W.batch_seed(WL.index) + 17 + seed_offset)
     smps = [O.OracleSample(WL.L, WL.n_temps, WL.t_min, WL.t_max, W.batch_seed(WL.index) + s,
-                           J=J[s].astype(np.float64), n_groups=WL.n_replicas, n_res=WL.n_res,
+                           J=J[s].astype(np.float64), n_groups=WL.n_replicas,
+                           n_res=WL.n_res if WL.er_on else 0, er_on=WL.er_on,
                            sweeps_per_emcs=WL.sweeps_per_emcs,
                            res_sweeps_per_emcs=WL.res_sweeps_per_emcs)
             for s in range(n_threads)]
@@ -154,7 +155,7 @@ def cpu_baseline():
     cores = os.cpu_count() or 1
     upd, dt, used = oracle_sample_run(cores)
     return {"value": upd / (dt * 1e9), "unit": UNIT, "cores": used, "kind": "oracle",
-            "sample": f"{used} samples x 1 EMCS of the L=16 workload (one sample per host thread), "
+            "sample": f"{used} samples x 1 EMCS of the L={WL.L} workload (one sample per host thread), "
                       f"{upd:.3g} spin updates in {dt:.1f} s"}
 
 
@@ -222,7 +223,8 @@ def run_gpu(args):
     J = W.gaussian_couplings(WL.L, S, W.batch_seed(WL.index) + rank)
     stream = torch.cuda.Stream(dev)
     b = Batch(cfg, couplings=J, seeds=seeds, device=dev, stream=stream)
-    b.prethermalize(WL.res_pretherm_sweeps)
+    if WL.er_on and WL.res_pretherm_sweeps:
+        b.prethermalize(WL.res_pretherm_sweeps)
     pt_upd, res_upd = updates_per_emcs(S)
     upd = pt_upd + res_upd
 
@@ -246,11 +248,11 @@ def run_gpu(args):
         for k in range(args.steps):
             e = ev[k]
             e[0].record(stream)
-            b.sweep(WL.sweeps_per_emcs, WL.res_sweeps_per_emcs)
+            b.sweep(WL.sweeps_per_emcs, WL.res_sweeps_per_emcs if WL.er_on else 0)
             e[1].record(stream)
             b.houdayer()
             e[2].record(stream)
-            b.swap(True, True)
+            b.swap(True, WL.er_on)
             e[3].record(stream)
             b.measure()
             e[4].record(stream)
@@ -303,7 +305,7 @@ def run_gpu(args):
         achieved_smem = SMEM_BYTES_PER_UPDATE * upd / (ms_sweep * 1e-3) / 1e12
         traffic = None
         tr_path = os.path.join(ROOT, "profiles", "sweep_kernel_L16_traffic.json")
-        if os.path.exists(tr_path):
+        if os.path.exists(tr_path) and WL is W.WORKLOADS["c4"]:
             with open(tr_path) as f:
                 tr = json.load(f)
             if tr.get("kernel_version") == kernel_version():
@@ -324,7 +326,7 @@ def run_gpu(args):
             "phase_ms": {"sweep": ms_sweep, "houdayer": float(phase[:, 1].mean()),
                          "swap": float(phase[:, 2].mean()), "measure": float(phase[:, 3].mean())},
             "plain": plain,
-            "roofline": {"kernel": "sweep_kernel<16, Metropolis>", "bound": "alu",
+            "roofline": {"kernel": f"sweep_kernel<{WL.L}, Metropolis>", "bound": "alu",
                          "achieved": achieved_ops, "peak": alu_peak, "unit": "Tops/s",
                          "frac": achieved_ops / alu_peak, "traffic": traffic,
                          "ops_per_update": OPS_PER_UPDATE,
@@ -366,7 +368,8 @@ def plain_form(dev, upd_per_sample, seeds, J, n=32):
     bs = [Batch(cfg, couplings=J[s:s + 1], seeds=seeds[s:s + 1], device=dev, stream=stream)
           for s in range(n)]
     for x in bs:
-        x.prethermalize(WL.res_pretherm_sweeps)
+        if WL.er_on and WL.res_pretherm_sweeps:
+            x.prethermalize(WL.res_pretherm_sweeps)
         x.emcs(1)
     stream.synchronize()
     t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -397,7 +400,8 @@ def end_to_end(dev, cfg, J, seeds, steps):
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
     b = Batch(cfg, couplings=Jp, seeds=seeds, device=dev, stream=stream)
-    b.prethermalize(WL.res_pretherm_sweeps)
+    if WL.er_on and WL.res_pretherm_sweeps:
+        b.prethermalize(WL.res_pretherm_sweeps)
     host = out.numpy()
     for _ in range(steps):
         b.emcs(1, graph=True)
@@ -405,7 +409,7 @@ def end_to_end(dev, cfg, J, seeds, steps):
     stream.synchronize()
     dt = time.perf_counter() - t0
     pt, res = updates_per_emcs(cfg.n_samples)
-    pre = cfg.n_samples * WL.n_replicas * WL.n_res * WL.res_pretherm_sweeps * WL.V
+    pre = cfg.n_samples * WL.n_replicas * WL.n_res * WL.res_pretherm_sweeps * WL.V if WL.er_on else 0
     b.close()
     return {"value": (steps * (pt + res) + pre) / (dt * 1e9), "unit": UNIT,
             "h2d_bytes_per_step": int((J.nbytes + seeds.nbytes) / steps),
@@ -473,6 +477,7 @@ def run_autotune(args):
 
 
 def main():
+    global WL
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=30)
@@ -491,7 +496,12 @@ def main():
                     help="advance all pools with one group graph per EMCS (admissions then "
                          "delay every pool, so per-pool stepping is the default)")
     ap.add_argument("--autotune", action="store_true", help="print the shape sweep for the workload")
+    ap.add_argument("--workload", default="c4", choices=["c2", "c3", "c4"],
+                    help="c4 (L=16 PTHR, the headline) or the batched L=8 / L=12 workloads")
     args = ap.parse_args()
+    WL = W.WORKLOADS[args.workload]
+    if args.samples == W.WORKLOADS["c4"].n_samples:
+        args.samples = WL.n_samples
     if args.serve:
         return run_serve(args)
     if args.autotune:
