@@ -78,6 +78,7 @@ __global__ void __launch_bounds__(512, 4) cluster_kernel(ClusterArgs a) {
     __shared__ int s_nneg, s_root, s_nclus, s_nflip;
     __shared__ int s_top[2][32];
     __shared__ double s_E[2];
+    __shared__ unsigned long long s_Ei[2];
     __shared__ int s_scan[1024];
 
     const Batch &b = a.b;
@@ -99,7 +100,7 @@ __global__ void __launch_bounds__(512, 4) cluster_kernel(ClusterArgs a) {
     uint32_t *gb_ptr = b.spins + ((size_t)s * b.NLAT + lb) * LW;
 
     if (tid == 0) { s_ok = 1; s_nneg = 0; s_root = -1; s_nclus = 0; s_nflip = 0; }
-    if (tid < 2) s_E[tid] = 0.0;
+    if (tid < 2) { s_E[tid] = 0.0; s_Ei[tid] = 0ull; }
     for (int i = tid; i < LW / 4; i += T) {
         reinterpret_cast<uint4 *>(sa)[i] = reinterpret_cast<const uint4 *>(ga_ptr)[i];
         reinterpret_cast<uint4 *>(sb)[i] = reinterpret_cast<const uint4 *>(gb_ptr)[i];
@@ -250,7 +251,7 @@ __global__ void __launch_bounds__(512, 4) cluster_kernel(ClusterArgs a) {
     if ((tid & 31) == 0) { s_top[0][tid >> 5] = t1; s_top[1][tid >> 5] = t2; }
     __syncthreads();
     // energies of both clones (Eq. (1)) over the forward bonds of every
-    // 4-site word, exact FP32 pairs per thread then FP64
+    // 4-site word: exact FP32 pairs per thread, then the sum over threads
     const float *J = b.J + (size_t)s * 3 * V;
     float ha = 0.f, la_ = 0.f, hb = 0.f, lb_ = 0.f;
     for (int w = tid; w < LW; w += T) {
@@ -278,20 +279,40 @@ __global__ void __launch_bounds__(512, 4) cluster_kernel(ClusterArgs a) {
             two_sum_acc(hb, lb_, Jz * spinf(pzB, kk));
         }
     }
-    double ea = (double)ha + (double)la_, eb = (double)hb + (double)lb_;
-    for (int o = 16; o > 0; o >>= 1) {
-        ea += __shfl_xor_sync(0xffffffffu, ea, o);
-        eb += __shfl_xor_sync(0xffffffffu, eb, o);
+    // When every thread's pair sums lie on the 2^-18 grid (couplings on the
+    // grid), the sum over threads runs exactly in integers; otherwise in FP64.
+    const float xa = ha * 262144.f, xla = la_ * 262144.f, xb = hb * 262144.f, xlb = lb_ * 262144.f;
+    const bool ig = xa == rintf(xa) && xla == rintf(xla) && xb == rintf(xb) && xlb == rintf(xlb) &&
+                    fabsf(xa) < 536870912.f && fabsf(xb) < 536870912.f && fabsf(xla) < 65536.f &&
+                    fabsf(xlb) < 65536.f;
+    const bool exact_E = __syncthreads_and(ig) != 0;
+    if (exact_E) {
+        const int va = __float2int_rn(xa) + __float2int_rn(xla);
+        const int vb = __float2int_rn(xb) + __float2int_rn(xlb);
+        // split so that the 32-lane sums cannot overflow
+        const int ah = __reduce_add_sync(0xffffffffu, va >> 12), bh = __reduce_add_sync(0xffffffffu, vb >> 12);
+        const unsigned al = __reduce_add_sync(0xffffffffu, (unsigned)(va & 0xFFF));
+        const unsigned bl = __reduce_add_sync(0xffffffffu, (unsigned)(vb & 0xFFF));
+        if ((tid & 31) == 0) {
+            atomicAdd(&s_Ei[0], (unsigned long long)((long long)ah * 4096 + (long long)al));
+            atomicAdd(&s_Ei[1], (unsigned long long)((long long)bh * 4096 + (long long)bl));
+        }
+    } else {
+        double ea = (double)ha + (double)la_, eb = (double)hb + (double)lb_;
+        for (int o = 16; o > 0; o >>= 1) {
+            ea += __shfl_xor_sync(0xffffffffu, ea, o);
+            eb += __shfl_xor_sync(0xffffffffu, eb, o);
+        }
+        if ((tid & 31) == 0) { atomicAdd(&s_E[0], ea); atomicAdd(&s_E[1], eb); }
     }
-    if ((tid & 31) == 0) { atomicAdd(&s_E[0], ea); atomicAdd(&s_E[1], eb); }
     __syncthreads();
     for (int i = tid; i < LW / 4; i += T) {
         reinterpret_cast<uint4 *>(ga_ptr)[i] = reinterpret_cast<const uint4 *>(sa)[i];
         reinterpret_cast<uint4 *>(gb_ptr)[i] = reinterpret_cast<const uint4 *>(sb)[i];
     }
     if (tid == 0) {
-        b.E[(size_t)s * b.NLAT + la] = -s_E[0];
-        b.E[(size_t)s * b.NLAT + lb] = -s_E[1];
+        b.E[(size_t)s * b.NLAT + la] = exact_E ? (double)(long long)s_Ei[0] * (-1.0 / 262144.0) : -s_E[0];
+        b.E[(size_t)s * b.NLAT + lb] = exact_E ? (double)(long long)s_Ei[1] * (-1.0 / 262144.0) : -s_E[1];
         int a1 = 0, a2 = 0;
         for (int w = 0; w < (T + 31) / 32; ++w) {
             const int u1 = s_top[0][w], u2 = s_top[1][w];

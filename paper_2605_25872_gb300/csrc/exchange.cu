@@ -79,9 +79,6 @@ __global__ void swap_kernel(Batch b, int flags, int first) {
     if (threadIdx.x == 0) b.emcs[s] = emcs + 1u;
 }
 
-// One block per (sample, temperature index k).  Accumulator layout per
-// (s, k): [0] measurements, [1] sum e, [2] sum e^2 (over groups), [3] sum q,
-// [4] sum q^2, [5] sum q_l, [6] sum S, [7] sum q^4 (over pairs).
 // Overlap counts of clones A and B on the packed colour-row layout: nneg =
 // number of sites with q_i = -1, ndiff = number of forward links (i, i+mu)
 // with q_i != q_{i+mu}.  One 32-bit word holds four same-colour sites; the
@@ -111,6 +108,16 @@ __device__ __forceinline__ void overlap_counts(const uint32_t *A, const uint32_t
     }
 }
 
+constexpr int MEASURE_MAX_WARPS = 8;   // threads per measurement block <= 256
+
+// One block per (sample, temperature index k).  Accumulator layout per
+// (s, k): [0] measurements, [1] sum e, [2] sum e^2 (over groups), [3] sum q,
+// [4] sum q^2, [5] sum q_l, [6] sum S, [7] sum q^4 (over pairs).
+//
+// Phase 1: every thread counts overlaps of every replica pair (and the chaos
+// pair); phase 2: warp 0 evaluates the FP64 quantities of the groups and
+// pairs on separate lanes, and lane 0 adds them to the accumulators in the
+// fixed order (groups, then pairs) with one IEEE rounding per operation.
 template <int L>
 __global__ void measure_kernel(Batch b, int first, int chaos) {
     using Gm = Geom<L>;
@@ -118,66 +125,75 @@ __global__ void measure_kernel(Batch b, int first, int chaos) {
     const int s = first + blockIdx.x;
     const int k = blockIdx.y;
     if (!b.active[s]) return;
-    __shared__ int s_neg[32], s_diff[32];
-    const int tid = threadIdx.x, T = blockDim.x;
-    double *o = b.obs + ((size_t)s * b.NT + k) * PTHR_NOBS;
-    const double Tk = temperature(b, k);
-    if (tid == 0) {
-        double se = o[1], se2 = o[2];
-        for (int g = 0; g < b.NR; ++g) {
-            const int lat = g * b.NSLOT + b.perm[((size_t)s * b.NR + g) * b.NSLOT + k];
-            const double e = __ddiv_rn(b.E[(size_t)s * b.NLAT + lat], (double)V);
-            se = __dadd_rn(se, e);
-            se2 = __dadd_rn(se2, __dmul_rn(e, e));
+    __shared__ int s_cnt[3][16][MEASURE_MAX_WARPS];   // [nneg, ndiff, chaos nneg][pair][warp]
+    const int tid = threadIdx.x, T = blockDim.x, lane = tid & 31, wid = tid >> 5;
+    const int32_t *perm = b.perm + (size_t)s * b.NR * b.NSLOT;
+    const uint32_t *spins = b.spins + (size_t)s * b.NLAT * LW;
+    for (int P = 0; P < b.NPAIR; ++P) {
+        const int la = 2 * P * b.NSLOT + perm[2 * P * b.NSLOT + k];
+        const int lb = (2 * P + 1) * b.NSLOT + perm[(2 * P + 1) * b.NSLOT + k];
+        int nneg, ndiff, cneg = 0;
+        overlap_counts<L>(spins + (size_t)la * LW, spins + (size_t)lb * LW, tid, T, nneg, ndiff);
+        if (chaos) {
+            // temperature chaos: clone of group 2P at T_0 against group 2P+1 at T_k
+            const int l0 = 2 * P * b.NSLOT + perm[2 * P * b.NSLOT];
+            int cdiff;
+            overlap_counts<L>(spins + (size_t)l0 * LW, spins + (size_t)lb * LW, tid, T, cneg, cdiff);
         }
+        nneg = __reduce_add_sync(0xffffffffu, nneg);
+        ndiff = __reduce_add_sync(0xffffffffu, ndiff);
+        cneg = __reduce_add_sync(0xffffffffu, cneg);
+        if (lane == 0) { s_cnt[0][P][wid] = nneg; s_cnt[1][P][wid] = ndiff; s_cnt[2][P][wid] = cneg; }
+    }
+    __syncthreads();
+    if (wid != 0) return;
+    // per-group energy density on lane g, per-pair overlaps on lane P
+    double e = 0.0, q = 0.0, ql = 0.0, S = 0.0, qc = 0.0;
+    if (lane < b.NR) {
+        const int lat = lane * b.NSLOT + perm[lane * b.NSLOT + k];
+        e = __ddiv_rn(b.E[(size_t)s * b.NLAT + lat], (double)V);
+    }
+    if (lane < b.NPAIR) {
+        int tn = 0, td = 0, tc = 0;
+        for (int w = 0; w < T / 32; ++w) { tn += s_cnt[0][lane][w]; td += s_cnt[1][lane][w]; tc += s_cnt[2][lane][w]; }
+        const double Tk = temperature(b, k);
+        const int la = 2 * lane * b.NSLOT + perm[2 * lane * b.NSLOT + k];
+        q = __ddiv_rn((double)(V - 2 * tn), (double)V);
+        ql = __ddiv_rn((double)(3 * V - 2 * td), 3.0 * (double)V);
+        const double Ha = b.E[(size_t)s * b.NLAT + la];
+        S = __dadd_rn(__ddiv_rn(Ha, 3.0 * (double)V), __ddiv_rn(__dsub_rn(1.0, ql), Tk));
+        qc = __ddiv_rn((double)(V - 2 * tc), (double)V);
+    }
+    double *o = b.obs + ((size_t)s * b.NT + k) * PTHR_NOBS;
+    double se = 0.0, se2 = 0.0;
+    if (lane == 0) { se = o[1]; se2 = o[2]; }
+    for (int g = 0; g < b.NR; ++g) {
+        const double eg = __shfl_sync(0xffffffffu, e, g);
+        if (lane == 0) {
+            se = __dadd_rn(se, eg);
+            se2 = __dadd_rn(se2, __dmul_rn(eg, eg));
+        }
+    }
+    if (lane == 0) {
         o[0] = __dadd_rn(o[0], 1.0);
         o[1] = se;
         o[2] = se2;
     }
+    double *c = b.chaos + ((size_t)s * b.NT + k) * 2;
     for (int P = 0; P < b.NPAIR; ++P) {
-        const int la = 2 * P * b.NSLOT + b.perm[((size_t)s * b.NR + 2 * P) * b.NSLOT + k];
-        const int lb = (2 * P + 1) * b.NSLOT + b.perm[((size_t)s * b.NR + 2 * P + 1) * b.NSLOT + k];
-        const uint32_t *A = b.spins + ((size_t)s * b.NLAT + la) * LW;
-        const uint32_t *B = b.spins + ((size_t)s * b.NLAT + lb) * LW;
-        int nneg, ndiff;
-        overlap_counts<L>(A, B, tid, T, nneg, ndiff);
-        nneg = __reduce_add_sync(0xffffffffu, nneg);
-        ndiff = __reduce_add_sync(0xffffffffu, ndiff);
-        if ((tid & 31) == 0) { s_neg[tid >> 5] = nneg; s_diff[tid >> 5] = ndiff; }
-        __syncthreads();
-        if (tid == 0) {
-            int tn = 0, td = 0;
-            for (int w = 0; w < T / 32; ++w) { tn += s_neg[w]; td += s_diff[w]; }
-            const double q = __ddiv_rn((double)(V - 2 * tn), (double)V);
-            const double ql = __ddiv_rn((double)(3 * V - 2 * td), 3.0 * (double)V);
-            const double Ha = b.E[(size_t)s * b.NLAT + la];
-            const double S = __dadd_rn(__ddiv_rn(Ha, 3.0 * (double)V), __ddiv_rn(__dsub_rn(1.0, ql), Tk));
-            const double q2 = __dmul_rn(q, q);
-            o[3] = __dadd_rn(o[3], q);
+        const double qP = __shfl_sync(0xffffffffu, q, P), qlP = __shfl_sync(0xffffffffu, ql, P);
+        const double SP = __shfl_sync(0xffffffffu, S, P), qcP = __shfl_sync(0xffffffffu, qc, P);
+        if (lane == 0) {
+            const double q2 = __dmul_rn(qP, qP);
+            o[3] = __dadd_rn(o[3], qP);
             o[4] = __dadd_rn(o[4], q2);
-            o[5] = __dadd_rn(o[5], ql);
-            o[6] = __dadd_rn(o[6], S);
-            o[7] = __dadd_rn(o[7], __dmul_rn(__dmul_rn(q2, q), q));
-        }
-        __syncthreads();
-        if (chaos) {
-            // temperature chaos: clone of group 2P at T_0 against group 2P+1 at T_k
-            const int l0 = 2 * P * b.NSLOT + b.perm[((size_t)s * b.NR + 2 * P) * b.NSLOT + 0];
-            const uint32_t *A0 = b.spins + ((size_t)s * b.NLAT + l0) * LW;
-            int cneg, cdiff;
-            overlap_counts<L>(A0, B, tid, T, cneg, cdiff);
-            cneg = __reduce_add_sync(0xffffffffu, cneg);
-            if ((tid & 31) == 0) s_neg[tid >> 5] = cneg;
-            __syncthreads();
-            if (tid == 0) {
-                int tn = 0;
-                for (int w = 0; w < T / 32; ++w) tn += s_neg[w];
-                const double q = __ddiv_rn((double)(V - 2 * tn), (double)V);
-                double *c = b.chaos + ((size_t)s * b.NT + k) * 2;
+            o[5] = __dadd_rn(o[5], qlP);
+            o[6] = __dadd_rn(o[6], SP);
+            o[7] = __dadd_rn(o[7], __dmul_rn(__dmul_rn(q2, qP), qP));
+            if (chaos) {
                 c[0] = __dadd_rn(c[0], 1.0);
-                c[1] = __dadd_rn(c[1], __dmul_rn(q, q));
+                c[1] = __dadd_rn(c[1], __dmul_rn(qcP, qcP));
             }
-            __syncthreads();
         }
     }
 }
@@ -198,8 +214,12 @@ cudaError_t launch_swap(const Batch &b, int flags, int first, int count, cudaStr
 }
 
 cudaError_t launch_measure(const Batch &b, int first, int count, int chaos, cudaStream_t st) {
+    if (b.NR > 32) return cudaErrorInvalidValue;
     dim3 grid(count, b.NT);
-#define X(LL) if (b.L == LL) { measure_kernel<LL><<<grid, 256, 0, st>>>(b, first, chaos); return cudaGetLastError(); }
+    // about two packed words per thread, 64..256 threads
+    int threads = ((lattice_words(b.L) / 2 + 31) / 32) * 32;
+    threads = threads < 64 ? 64 : (threads > 32 * MEASURE_MAX_WARPS ? 32 * MEASURE_MAX_WARPS : threads);
+#define X(LL) if (b.L == LL) { measure_kernel<LL><<<grid, threads, 0, st>>>(b, first, chaos); return cudaGetLastError(); }
     PTHR_FOR_EACH_L(X)
 #undef X
     return cudaErrorInvalidValue;

@@ -75,9 +75,109 @@ __device__ __forceinline__ f2 mul2(f2 a, f2 b) {
     asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
     return d;
 }
+__device__ __forceinline__ f2 add2(f2 a, f2 b) {
+    f2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2 sub2(f2 a, f2 b) {
+    f2 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+// Knuth's TwoSum on both halves: hi + lo stays the exact running sum while
+// lo does not round.
+__device__ __forceinline__ void two_sum2(f2 &hi, f2 &lo, f2 t) {
+    const f2 s = add2(hi, t);
+    const f2 bb = sub2(s, hi);
+    lo = add2(lo, add2(sub2(hi, sub2(s, bb)), sub2(t, bb)));
+    hi = s;
+}
 // spins of sites 2h and 2h+1 of a product word as a packed pair
 __device__ __forceinline__ f2 spin_pair(uint32_t w, int h) {
     return pack2(spinf(w, 2 * h), spinf(w, 2 * h + 1));
+}
+
+// A coupling on the 2^-18 grid with |J| <= 8: then every partial sum of at
+// most six terms +-J is a multiple of 2^-18 below 64 in magnitude, which
+// FP32 holds exactly, and so is every local field.
+__device__ __forceinline__ bool on_coupling_grid(float j) {
+    const float y = j * 262144.f;
+    return fabsf(j) <= 8.f && y == rintf(y);
+}
+
+// Couplings of the four sites of group g, colour c, in the order +x, -x, +y,
+// -y, +z, -z, times `scale`, as packed pairs (sites 0,1 and 2,3); row padding
+// sites get zero couplings.
+template <int L>
+__device__ __forceinline__ void group_couplings(const float *Js, const GroupGeo &q, int g, int c,
+                                                float scale, f2 (&Jp)[2][6]) {
+    using Gm = Geom<L>;
+    constexpr int W = Gm::W, ROWS = Gm::ROWS, Lh = Gm::Lh, LB = Gm::LAT_BYTES;
+    const int j = g % W, r = g / W;
+    const int y = r % L, z = r / L, cc = c ^ 1;
+    const int rym = ((y + L - 1) % L) + L * z, rzm = y + L * ((z + L - 1) % L);
+    float Jc[4][6];
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk) {
+        int m = 4 * j + kk;
+        const bool pad = !Gm::FULL && m >= Lh;
+        if (pad) m = Lh - 1;
+        const int so = 4 * q.own + kk;
+        const int mxm = q.par ? m : (m + Lh - 1) % Lh;
+        const float f = pad ? 0.f : scale;
+        Jc[kk][0] = f * Js[so];
+        Jc[kk][1] = f * Js[4 * ((cc * ROWS + r) * W) + mxm];
+        Jc[kk][2] = f * Js[LB + so];
+        Jc[kk][3] = f * Js[LB + 4 * ((cc * ROWS + rym) * W) + m];
+        Jc[kk][4] = f * Js[2 * LB + so];
+        Jc[kk][5] = f * Js[2 * LB + 4 * ((cc * ROWS + rzm) * W) + m];
+    }
+#pragma unroll
+    for (int n = 0; n < 6; ++n) {
+        Jp[0][n] = pack2(Jc[0][n], Jc[1][n]);
+        Jp[1][n] = pack2(Jc[2][n], Jc[3][n]);
+    }
+}
+
+// t_i = sum_j J_ij s_i s_j of the four sites of group q of lattice S, as two
+// packed pairs, in the fixed order +x, -x, +y, -y, +z, -z.
+__device__ __forceinline__ void group_fields(const uint32_t *S, const GroupGeo &q,
+                                             const f2 (&Jp)[2][6], f2 (&tt)[2]) {
+    const uint32_t own = S[q.own];
+    const uint32_t xa = S[q.xa];
+    const uint32_t xs = __byte_perm(S[q.wA], S[q.wB], q.selx);
+    const uint32_t wxp = q.par ? xs : xa, wxm = q.par ? xa : xs;
+    const uint32_t X = 0x3F3F3F3Fu;
+    const uint32_t pxp = own ^ wxp ^ X, pxm = own ^ wxm ^ X;
+    const uint32_t pyp = own ^ S[q.yp] ^ X, pym = own ^ S[q.ym] ^ X;
+    const uint32_t pzp = own ^ S[q.zp] ^ X, pzm = own ^ S[q.zm] ^ X;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        f2 t = mul2(Jp[h][0], spin_pair(pxp, h));
+        t = fma2(Jp[h][1], spin_pair(pxm, h), t);
+        t = fma2(Jp[h][2], spin_pair(pyp, h), t);
+        t = fma2(Jp[h][3], spin_pair(pym, h), t);
+        t = fma2(Jp[h][4], spin_pair(pzp, h), t);
+        tt[h] = fma2(Jp[h][5], spin_pair(pzm, h), t);
+    }
+}
+
+// Sums w and f over the lanes of this warp that share this thread's lattice
+// lane (a contiguous run of lanes: group index g0 within a lane of Gt
+// groups); the run's first lane (lane 0 or g0 == 0) holds the result.  nl =
+// lanes present in the warp, wmask = their mask.
+__device__ __forceinline__ void segment_sum(long long &w, unsigned &f, int lane, int nl, int g0,
+                                            int Gt, unsigned wmask) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long wu = __shfl_down_sync(wmask, w, o);
+        const unsigned fu = __shfl_down_sync(wmask, f, o);
+        if (lane + o < nl && g0 + o < Gt) {
+            w += wu;
+            f += fu;
+        }
+    }
 }
 
 template <int L, int RULE, int KT>
@@ -92,6 +192,7 @@ __global__ void __launch_bounds__(512) sweep_kernel(SweepArgs a) {
     __shared__ float s_tb[MAXK];
     __shared__ unsigned int s_flips[MAXK];
     __shared__ double s_E[MAXK];
+    __shared__ unsigned long long s_Ei[MAXK];
 
     const Batch &b = a.b;
     // ---- decode the task
@@ -135,30 +236,70 @@ __global__ void __launch_bounds__(512) sweep_kernel(SweepArgs a) {
         s_tb[tid] = (float)(-2.0 * 1.4426950408889634073599 / T_k);
         s_flips[tid] = 0u;
         s_E[tid] = 0.0;
+        s_Ei[tid] = 0ull;
     }
-    // ---- couplings -> shared memory, packed colour-row layout
+    // ---- couplings -> shared memory, packed colour-row layout; several
+    // loads in flight per thread.  Note whether all of them lie on the 2^-18
+    // grid with |J| <= 8 (then the energies are summed exactly in integers).
     const float *Jg = b.J + (size_t)s * 3 * Gm::V;
-    if (!Gm::FULL) {
+    if (!Gm::FULL)
         for (int i = tid; i < 3 * LB; i += T) Js[i] = 0.f;
-        __syncthreads();
+    __syncthreads();     // lattice ids and zeroed row padding visible
+    bool on_grid = true;
+    constexpr int JU = 4;
+    for (int i0 = tid; i0 < Gm::V; i0 += JU * T) {
+        float jv[JU][3];
+#pragma unroll
+        for (int u = 0; u < JU; ++u) {
+            const int i = i0 + u * T;
+            if (i < Gm::V) {
+                jv[u][0] = __ldg(Jg + i);
+                jv[u][1] = __ldg(Jg + Gm::V + i);
+                jv[u][2] = __ldg(Jg + 2 * Gm::V + i);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < JU; ++u) {
+            const int i = i0 + u * T;
+            if (i < Gm::V) {
+                int w, by;
+                site_slot<L>(i, w, by);
+                const int slot = 4 * w + by;
+                Js[slot] = jv[u][0];
+                Js[LB + slot] = jv[u][1];
+                Js[2 * LB + slot] = jv[u][2];
+                on_grid = on_grid && on_coupling_grid(jv[u][0]) && on_coupling_grid(jv[u][1]) &&
+                          on_coupling_grid(jv[u][2]);
+            }
+        }
     }
-    for (int i = tid; i < Gm::V; i += T) {
-        int w, by;
-        site_slot<L>(i, w, by);
-        const int slot = 4 * w + by;
-        Js[slot] = Jg[i];
-        Js[LB + slot] = Jg[Gm::V + i];
-        Js[2 * LB + slot] = Jg[2 * Gm::V + i];
+    // ---- spins -> shared memory: all K lattices in one flat loop
+    {
+        constexpr int LQ = LW / 4;
+        const int nq = K * LQ;
+        constexpr int SU = 4;
+        for (int i0 = tid; i0 < nq; i0 += SU * T) {
+            uint4 v[SU];
+#pragma unroll
+            for (int u = 0; u < SU; ++u) {
+                const int i = i0 + u * T;
+                if (i < nq) {
+                    const int k = i / LQ;
+                    v[u] = reinterpret_cast<const uint4 *>(
+                        b.spins + ((size_t)s * b.NLAT + s_lat[k]) * LW)[i - k * LQ];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < SU; ++u) {
+                const int i = i0 + u * T;
+                if (i < nq) {
+                    const int k = i / LQ;
+                    reinterpret_cast<uint4 *>(Ss + k * LW)[i - k * LQ] = v[u];
+                }
+            }
+        }
     }
-    __syncthreads();
-    // ---- spins -> shared memory
-    for (int k = 0; k < K; ++k) {
-        const uint4 *src = reinterpret_cast<const uint4 *>(
-            b.spins + ((size_t)s * b.NLAT + s_lat[k]) * LW);
-        uint4 *dst = reinterpret_cast<uint4 *>(Ss + k * LW);
-        for (int i = tid; i < LW / 4; i += T) dst[i] = src[i];
-    }
-    __syncthreads();
+    const bool exact_E = __syncthreads_and(on_grid) != 0;
 
     const int Gt = a.Gt;                 // groups per lattice lane pass (divides G)
     const int lane_p = tid / Gt, g0 = tid - lane_p * Gt;
@@ -280,63 +421,132 @@ __global__ void __launch_bounds__(512) sweep_kernel(SweepArgs a) {
         }
     }
 
-    // ---- energies (Eq. (1)) of the swept lattices: each thread sums the
-    // forward bonds of its sites exactly in FP32 pairs, then FP64 reduction.
+    // ---- energies (Eq. (1)) of the swept lattices and their flip counts
+    const int lane = tid & 31;
+    const int nl = min(32, T - (tid & ~31));                  // lanes of this warp
+    const unsigned wmask = nl == 32 ? 0xffffffffu : ((1u << nl) - 1u);
+    if (exact_E) {
+        // Every bond joins the two colours, so H = -(sum of t_i over the
+        // colour-0 sites).  With the couplings scaled by 2^18 every t_i is an
+        // integer below 2^24 in FP32, the packed TwoSum keeps each thread's
+        // sum exact, and the sum over threads runs in integers.
+        constexpr bool ONE = G <= 512;   // then Gt = G: one group per thread
+        GroupGeo q1{};
+        f2 J1[2][6];
+        if (ONE) {
+            q1 = group_geo<L>(g0, 0);
+            group_couplings<L>(Js, q1, g0, 0, 262144.f, J1);
+        }
 #pragma unroll
-    for (int jj = 0; jj < KT; ++jj) {
-        const int k = kbase + jj;
-        const bool mine = k < K;
-        float hi = 0.f, lo = 0.f;
-        if (mine) {
-            const uint32_t *S = Sb + jj * LW;
-            for (int gi = 0; gi < GP; ++gi) {
-                const int g = g0 + gi * Gt;
-                const int j = g % W;
-                for (int c = 0; c < 2; ++c) {
-                    const GroupGeo q = group_geo<L>(g, c);
-                    const uint32_t own = S[q.own];
-                    const uint32_t xa = S[q.xa];
-                    const uint32_t xs = __byte_perm(S[q.wA], S[q.wB], q.selx);
-                    const uint32_t wxp = q.par ? xs : xa;
-                    const uint32_t wyp = S[q.yp], wzp = S[q.zp];
-#pragma unroll
-                    for (int kk = 0; kk < 4; ++kk) {
-                        if (!Gm::FULL && 4 * j + kk >= Lh) continue;
-                        const int so = 4 * q.own + kk;
-                        const float si = spinf(own, kk);
-                        two_sum_acc(hi, lo, si * (Js[so] * spinf(wxp, kk)));
-                        two_sum_acc(hi, lo, si * (Js[LB + so] * spinf(wyp, kk)));
-                        two_sum_acc(hi, lo, si * (Js[2 * LB + so] * spinf(wzp, kk)));
+        for (int jj = 0; jj < KT; ++jj) {
+            const int k = kbase + jj;
+            const bool mine = k < K;
+            int v = 0;
+            if (mine) {
+                const uint32_t *S = Sb + jj * LW;
+                f2 hi = 0ull, lo = 0ull, tt[2];
+                if (ONE) {
+                    group_fields(S, q1, J1, tt);
+                    hi = tt[0];
+                    two_sum2(hi, lo, tt[1]);
+                } else {
+                    for (int gi = 0; gi < GP; ++gi) {
+                        const int g = g0 + gi * Gt;
+                        const GroupGeo q = group_geo<L>(g, 0);
+                        f2 Jq[2][6];
+                        group_couplings<L>(Js, q, g, 0, 262144.f, Jq);
+                        group_fields(S, q, Jq, tt);
+                        two_sum2(hi, lo, tt[0]);
+                        two_sum2(hi, lo, tt[1]);
                     }
+                }
+                float h0, h1, l0, l1;
+                unpack2(hi, h0, h1);
+                unpack2(lo, l0, l1);
+                v = __float2int_rn(h0) + __float2int_rn(h1) + __float2int_rn(l0) + __float2int_rn(l1);
+            }
+            unsigned nf = nfl[jj];
+            if (warp_uniform) {
+                // every lane of a warp has the same lattice lane, hence the same
+                // k; split v so that the 32-lane sums cannot overflow
+                const int shi = __reduce_add_sync(0xffffffffu, v >> 12);
+                const unsigned slo = __reduce_add_sync(0xffffffffu, (unsigned)(v & 0xFFF));
+                nf = __reduce_add_sync(0xffffffffu, nf);
+                if (lane == 0 && mine) {
+                    atomicAdd(&s_Ei[k], (unsigned long long)((long long)shi * 4096 + (long long)slo));
+                    atomicAdd(&s_flips[k], nf);
+                }
+            } else {
+                long long w = v;
+                segment_sum(w, nf, lane, nl, g0, Gt, wmask);
+                if ((lane == 0 || g0 == 0) && mine) {
+                    atomicAdd(&s_Ei[k], (unsigned long long)w);
+                    atomicAdd(&s_flips[k], nf);
                 }
             }
         }
-        double v = (double)hi + (double)lo;
-        unsigned nf = nfl[jj];
-        if (warp_uniform) {
-            // every lane of a warp has the same lattice lane, hence the same k
+    } else {
+        // couplings off the grid: each thread sums the forward bonds of its
+        // sites in FP32 TwoSum pairs, then FP64 reduction
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-            nf = __reduce_add_sync(0xffffffffu, nf);
-            if ((tid & 31) == 0 && mine) {
+        for (int jj = 0; jj < KT; ++jj) {
+            const int k = kbase + jj;
+            const bool mine = k < K;
+            float hi = 0.f, lo = 0.f;
+            if (mine) {
+                const uint32_t *S = Sb + jj * LW;
+                for (int gi = 0; gi < GP; ++gi) {
+                    const int g = g0 + gi * Gt;
+                    const int j = g % W;
+                    for (int c = 0; c < 2; ++c) {
+                        const GroupGeo q = group_geo<L>(g, c);
+                        const uint32_t own = S[q.own];
+                        const uint32_t xa = S[q.xa];
+                        const uint32_t xs = __byte_perm(S[q.wA], S[q.wB], q.selx);
+                        const uint32_t wxp = q.par ? xs : xa;
+                        const uint32_t wyp = S[q.yp], wzp = S[q.zp];
+#pragma unroll
+                        for (int kk = 0; kk < 4; ++kk) {
+                            if (!Gm::FULL && 4 * j + kk >= Lh) continue;
+                            const int so = 4 * q.own + kk;
+                            const float si = spinf(own, kk);
+                            two_sum_acc(hi, lo, si * (Js[so] * spinf(wxp, kk)));
+                            two_sum_acc(hi, lo, si * (Js[LB + so] * spinf(wyp, kk)));
+                            two_sum_acc(hi, lo, si * (Js[2 * LB + so] * spinf(wzp, kk)));
+                        }
+                    }
+                }
+            }
+            double v = (double)hi + (double)lo;
+            unsigned nf = nfl[jj];
+            if (warp_uniform) {
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                nf = __reduce_add_sync(0xffffffffu, nf);
+                if (lane == 0 && mine) {
+                    atomicAdd(&s_E[k], v);
+                    atomicAdd(&s_flips[k], nf);
+                }
+            } else if (mine) {
                 atomicAdd(&s_E[k], v);
                 atomicAdd(&s_flips[k], nf);
             }
-        } else if (mine) {
-            atomicAdd(&s_E[k], v);
-            atomicAdd(&s_flips[k], nf);
         }
     }
     __syncthreads();
-    // ---- write back
-    for (int k = 0; k < K; ++k) {
-        uint4 *dst = reinterpret_cast<uint4 *>(b.spins + ((size_t)s * b.NLAT + s_lat[k]) * LW);
-        const uint4 *src = reinterpret_cast<const uint4 *>(Ss + k * LW);
-        for (int i = tid; i < LW / 4; i += T) dst[i] = src[i];
+    // ---- write back: one flat loop over all K lattices
+    {
+        constexpr int LQ = LW / 4;
+        const int nq = K * LQ;
+        for (int i = tid; i < nq; i += T) {
+            const int k = i / LQ;
+            reinterpret_cast<uint4 *>(b.spins + ((size_t)s * b.NLAT + s_lat[k]) * LW)[i - k * LQ] =
+                reinterpret_cast<const uint4 *>(Ss + k * LW)[i - k * LQ];
+        }
     }
     if (tid < K) {
         const size_t li = (size_t)s * b.NLAT + s_lat[tid];
-        b.E[li] = -s_E[tid];
+        b.E[li] = exact_E ? (double)(long long)s_Ei[tid] * (-1.0 / 262144.0) : -s_E[tid];
         if (s_flips[tid]) atomicAdd(&b.flips[li], (unsigned long long)s_flips[tid]);
     }
 }
