@@ -36,8 +36,10 @@ def candidates(cfg: BatchConfig):
     kr = sorted({k for k in (2, 4, 8, 16, 32) if k <= nres} | {nres if nres <= 64 else 64})
     for kp, krs in itertools.product(ks, kr):
         yield {"pt_lattices_per_block": kp, "res_lattices_per_block": krs}
-    for ct in (128, 256, 384):
-        yield {"cluster_threads": ct}
+    V = cfg.L ** 3
+    for ct in (64, 128, 256, 384, 512):
+        if ct <= max(64, V // 2):
+            yield {"cluster_threads": ct}
 
 
 def time_shape(b: Batch, shape: dict, emcs: int = 3, warmup: int = 1) -> float:

@@ -216,6 +216,13 @@ pthr_status do_sweep(pthr_batch *b, int n_pt, int n_res, int first, int count, i
     return PTHR_OK;
 }
 
+// Threads per cluster-move block: about eight sites per thread, 128..512.
+int default_cluster_threads(int L) {
+    const int V = L * L * L;
+    int t = ((V / 8 + 31) / 32) * 32;
+    return t < 128 ? 128 : (t > 512 ? 512 : t);
+}
+
 pthr_status do_cluster(pthr_batch *b, int label_only, int32_t *labels) {
     if (b->dev.n_acu == 0 && !label_only) return PTHR_OK;
     ClusterArgs a{};
@@ -229,7 +236,7 @@ pthr_status do_cluster(pthr_batch *b, int label_only, int32_t *labels) {
     a.label_only = label_only;
     a.labels_out = labels;
     a.iter_cap = b->tuning.cluster_iter_cap;
-    int threads = b->tuning.cluster_threads > 0 ? b->tuning.cluster_threads : 512;
+    int threads = b->tuning.cluster_threads > 0 ? b->tuning.cluster_threads : default_cluster_threads(b->cfg.L);
     const int V = b->cfg.L * b->cfg.L * b->cfg.L;
     if (threads > ((V + 31) / 32) * 32) threads = ((V + 31) / 32) * 32;
     if (threads < 32) threads = 32;
@@ -408,7 +415,7 @@ PTHR_API pthr_status pthr_get_tuning(const pthr_batch *b, pthr_tuning *t) {
     t->pt_lattices_per_block = sh.K_pt;
     t->res_lattices_per_block = sh.K_res;
     t->sweep_threads = sh.threads;
-    t->cluster_threads = b->tuning.cluster_threads > 0 ? b->tuning.cluster_threads : 512;
+    t->cluster_threads = b->tuning.cluster_threads > 0 ? b->tuning.cluster_threads : default_cluster_threads(b->cfg.L);
     t->cluster_iter_cap = b->tuning.cluster_iter_cap;
     return PTHR_OK;
 }

@@ -12,10 +12,12 @@
 //     root is the smallest site index of its cluster (the canonical label).
 //     An edge whose left neighbours in both rows are in the same two runs is
 //     implied by that neighbouring edge and skipped; x = 0 never skips.
-// One sign per root is drawn from Philox keyed by the label; both clones flip
-// word by word, both energies are recomputed in FP64 (exact FP32 pairs per
-// thread) and the pair is written back.  Every loop is bounded; hitting a
-// bound sets STATUS_NOCONVERGE instead of spinning.
+// The q values of a row are one bit mask, so runs and the edges to join come
+// from a few bit operations per row.  One sign per root is drawn from Philox
+// keyed by the label; both clones flip word by word, the energies are updated
+// (on the coupling grid H_a is recomputed and H_b follows from the conserved
+// H_a + H_b) and the pair is written back.  Every loop is bounded; hitting a bound sets STATUS_NOCONVERGE
+// instead of spinning.
 #include "kernels.cuh"
 #include "geometry.cuh"
 
@@ -47,6 +49,15 @@ __device__ __forceinline__ void unite(volatile int *parent, int a, int b, int ca
     ok = false;
 }
 
+// bit m of v -> bit 2m (m < 16)
+__device__ __forceinline__ uint32_t spread_bits(uint32_t v) {
+    v = (v | (v << 8)) & 0x00FF00FFu;
+    v = (v | (v << 4)) & 0x0F0F0F0Fu;
+    v = (v | (v << 2)) & 0x33333333u;
+    v = (v | (v << 1)) & 0x55555555u;
+    return v;
+}
+
 // natural site index of byte kk of packed word w
 template <int L>
 __device__ __forceinline__ int site_of_word(int w, int kk) {
@@ -58,6 +69,51 @@ __device__ __forceinline__ int site_of_word(int w, int kk) {
     const int y = r % L, z = r / L;
     const int x = 2 * (4 * j + kk) + ((c + y + z) & 1);
     return x + L * r;
+}
+
+// FP32 TwoSum pair (h, l) of this thread's share of sum_i sum_mu J_{i,mu}
+// s_i s_{i+mu} over the forward bonds of clone S (packed layout).  Every term
+// +-J is exact; h + l is the exact sum while l does not round.
+// With S2 set, the same for a second clone into (*h2, *l2) in the same pass.
+template <int L>
+__device__ __forceinline__ void clone_energy_pairs(const uint32_t *S, const float *J, int tid, int T,
+                                                   float &h, float &l, const uint32_t *S2 = nullptr,
+                                                   float *h2 = nullptr, float *l2 = nullptr) {
+    using Gm = Geom<L>;
+    constexpr int V = Gm::V, LW = Gm::LAT_WORDS, W = Gm::W, Lh = Gm::Lh;
+    for (int w = tid; w < LW; w += T) {
+        const int c = w / (Gm::ROWS * W);
+        const int g = w - c * Gm::ROWS * W;
+        const GroupGeo q = group_geo<L>(g, c);
+        const int j = g % W;
+        const uint32_t X = 0x3F3F3F3Fu;
+        const uint32_t o = S[q.own];
+        const uint32_t x = q.par ? __byte_perm(S[q.wA], S[q.wB], q.selx) : S[q.xa];
+        // bytes 0x3F where s_i s_{i+mu} = +1, 0xBF where -1
+        const uint32_t px = o ^ x ^ X, py = o ^ S[q.yp] ^ X, pz = o ^ S[q.zp] ^ X;
+        uint32_t px2 = 0, py2 = 0, pz2 = 0;
+        if (S2) {
+            const uint32_t o2 = S2[q.own];
+            const uint32_t x2 = q.par ? __byte_perm(S2[q.wA], S2[q.wB], q.selx) : S2[q.xa];
+            px2 = o2 ^ x2 ^ X;
+            py2 = o2 ^ S2[q.yp] ^ X;
+            pz2 = o2 ^ S2[q.zp] ^ X;
+        }
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+            if (!Gm::FULL && 4 * j + kk >= Lh) continue;
+            const int i = site_of_word<L>(w, kk);
+            const float Jx = J[i], Jy = J[V + i], Jz = J[2 * V + i];
+            two_sum_acc(h, l, Jx * spinf(px, kk));
+            two_sum_acc(h, l, Jy * spinf(py, kk));
+            two_sum_acc(h, l, Jz * spinf(pz, kk));
+            if (S2) {
+                two_sum_acc(*h2, *l2, Jx * spinf(px2, kk));
+                two_sum_acc(*h2, *l2, Jy * spinf(py2, kk));
+                two_sum_acc(*h2, *l2, Jz * spinf(pz2, kk));
+            }
+        }
+    }
 }
 
 // CAPPED = false: every loop bound is the compile-time constant 4V+64 (the
@@ -73,12 +129,13 @@ __global__ void __launch_bounds__(512, 4) cluster_kernel(ClusterArgs a) {
     int *cnt = parent + V;                                             // [V]
     uint32_t *sa = reinterpret_cast<uint32_t *>(cnt + V);              // [LW]
     uint32_t *sb = sa + LW;                                            // [LW]
-    unsigned char *flag = reinterpret_cast<unsigned char *>(sb + LW);  // [V] q bit, later root flag
+    unsigned char *flag = reinterpret_cast<unsigned char *>(sb + LW);  // [V] sign of each root
+    uint32_t *qrow = reinterpret_cast<uint32_t *>(flag + ((V + 3) & ~3));  // [L*L] q bits per x row
     __shared__ int s_ok;
     __shared__ int s_nneg, s_root, s_nclus, s_nflip;
     __shared__ int s_top[2][32];
     __shared__ double s_E[2];
-    __shared__ unsigned long long s_Ei[2];
+    __shared__ unsigned long long s_Ei[1];
     __shared__ int s_scan[1024];
 
     const Batch &b = a.b;
@@ -100,52 +157,69 @@ __global__ void __launch_bounds__(512, 4) cluster_kernel(ClusterArgs a) {
     uint32_t *gb_ptr = b.spins + ((size_t)s * b.NLAT + lb) * LW;
 
     if (tid == 0) { s_ok = 1; s_nneg = 0; s_root = -1; s_nclus = 0; s_nflip = 0; }
-    if (tid < 2) { s_E[tid] = 0.0; s_Ei[tid] = 0ull; }
+    if (tid < 2) s_E[tid] = 0.0;
+    if (tid == 0) s_Ei[0] = 0ull;
     for (int i = tid; i < LW / 4; i += T) {
         reinterpret_cast<uint4 *>(sa)[i] = reinterpret_cast<const uint4 *>(ga_ptr)[i];
         reinterpret_cast<uint4 *>(sb)[i] = reinterpret_cast<const uint4 *>(gb_ptr)[i];
     }
     __syncthreads();
-    // q_i < 0 <=> the two bytes differ (0x3F vs 0xBF): one XOR per 4 sites
-    for (int w = tid; w < LW; w += T) {
-        const uint32_t qw = sa[w] ^ sb[w];
-        const int j = (w % (Gm::ROWS * W)) % W;
+    // q bits of every natural x row r = y + L z: bit x of qrow[r] is 1 iff
+    // q_i = -1 at i = x + L r.  The two clones' bytes differ exactly there
+    // (0x3F vs 0xBF): one XOR per 4 sites, a multiply gathers the four sign
+    // bits, and the two colour rows interleave (colour c holds x = 2m + p_c).
+    constexpr uint32_t M = L == 32 ? 0xffffffffu : ((1u << L) - 1u);
+    for (int r = tid; r < L * L; r += T) {
+        const int y = r % L, z = r / L;
+        uint32_t bits[2];
 #pragma unroll
-        for (int kk = 0; kk < 4; ++kk) {
-            if (!Gm::FULL && 4 * j + kk >= Lh) continue;
-            const int i = site_of_word<L>(w, kk);
-            flag[i] = (unsigned char)((qw >> (8 * kk + 7)) & 1u);
-            cnt[i] = 0;
+        for (int c = 0; c < 2; ++c) {
+            uint32_t acc = 0;
+#pragma unroll
+            for (int j = 0; j < W; ++j) {
+                const int w = (c * Gm::ROWS + r) * W + j;
+                const uint32_t qw = (sa[w] ^ sb[w]) & 0x80808080u;
+                acc |= ((qw * 0x00204081u) >> 28) << (4 * j);
+            }
+            bits[c] = acc & ((1u << Lh) - 1u);
         }
+        const int p0 = (y + z) & 1;
+        qrow[r] = (spread_bits(bits[0]) << p0) | (spread_bits(bits[1]) << (p0 ^ 1));
     }
+    for (int i = tid; i < V; i += T) cnt[i] = 0;
     __syncthreads();
-    // 1. runs of equal q along each periodic x row, rooted at their first site
+    // 1. runs of equal q along each periodic x row, rooted at their first
+    //    site; the last run is rooted at x = 0 when it wraps onto the first
     for (int r = tid; r < L * L; r += T) {
         const int i0 = L * r;
-        parent[i0] = i0;
-        for (int x = 1; x < L; ++x) {
-            const int i = i0 + x;
-            parent[i] = (flag[i] == flag[i - 1]) ? parent[i - 1] : i;
-        }
-        if (flag[i0 + L - 1] == flag[i0]) {     // the last run wraps onto the first
-            const int last = parent[i0 + L - 1];
-            if (last != i0)
-                for (int x = L - 1; x > 0 && parent[i0 + x] == last; --x) parent[i0 + x] = i0;
+        const uint32_t q = qrow[r];
+        const uint32_t st = (q ^ (q << 1)) & M & ~1u;       // bit x >= 1: q[x] != q[x-1]
+        const bool wrap = ((q ^ (q >> (L - 1))) & 1u) == 0u;  // q[0] == q[L-1]
+        const int last = st ? 31 - __clz(st) : L;            // start of the last run
+        int root = i0;
+        for (int x = 0; x < L; ++x) {
+            if ((st >> x) & 1u) root = i0 + x;
+            parent[i0 + x] = (wrap && x >= last) ? i0 : root;
         }
     }
     __syncthreads();
-    // 2. join runs across y and z edges
+    // 2. join runs across y and z edges, one thread per (row, direction).
+    //    Edges join equal q; an edge at x != 0 where no run starts in either
+    //    row is implied by the edge at x - 1 and skipped.
     bool ok = true;
     const int cap = CAPPED ? a.iter_cap : 4 * V + 64;
     volatile int *vp = parent;
-    for (int i = tid; i < V; i += T) {
-        const int x = i % L, y = (i / L) % L, z = i / (L * L);
-        const unsigned char qi = flag[i];
-        const bool left_same = x != 0 && flag[i - 1] == qi;
-        const int jy = x + L * (((y + 1) % L) + L * z);
-        const int jz = x + L * (y + L * ((z + 1) % L));
-        if (flag[jy] == qi && !(left_same && flag[jy - 1] == qi)) unite(vp, i, jy, cap, ok);
-        if (flag[jz] == qi && !(left_same && flag[jz - 1] == qi)) unite(vp, i, jz, cap, ok);
+    for (int tsk = tid; tsk < 2 * L * L; tsk += T) {
+        const int r = tsk >> 1;
+        const int y = r % L, z = r / L;
+        const int r2 = (tsk & 1) ? y + L * ((z + 1) % L) : ((y + 1) % L) + L * z;
+        const uint32_t q1 = qrow[r], q2 = qrow[r2];
+        uint32_t C = ~(q1 ^ q2) & M & ((q1 ^ (q1 << 1)) | (q2 ^ (q2 << 1)) | 1u);
+        while (C) {
+            const int x = __ffs(C) - 1;
+            C &= C - 1u;
+            unite(vp, L * r + x, L * r2 + x, cap, ok);
+        }
     }
     __syncthreads();
     for (int i = tid; i < V; i += T) {
@@ -183,11 +257,12 @@ __global__ void __launch_bounds__(512, 4) cluster_kernel(ClusterArgs a) {
         }
         __syncthreads();
     } else {
-        // single cluster: seed = the floor(u*n)-th q = -1 site, n = #(q = -1)
-        const int chunk = (V + T - 1) / T;
-        const int lo = tid * chunk, hi = min(V, lo + chunk);
+        // single cluster: seed = the floor(u*n)-th q = -1 site (natural
+        // order), n = #(q = -1); each thread counts a contiguous range of rows
+        const int chunk = (L * L + T - 1) / T;
+        const int lo = min(L * L, tid * chunk), hi = min(L * L, lo + chunk);
         int my = 0;
-        for (int i = lo; i < hi; ++i) my += flag[i];
+        for (int r = lo; r < hi; ++r) my += __popc(qrow[r]);
         s_scan[tid] = my;
         __syncthreads();
         if (tid == 0) {
@@ -202,11 +277,15 @@ __global__ void __launch_bounds__(512, 4) cluster_kernel(ClusterArgs a) {
             const int target = (int)(((unsigned long long)(w >> 8) * (unsigned long long)n) >> 24);
             int seen = s_scan[tid];
             if (target >= seen && target < seen + my) {
-                for (int i = lo; i < hi; ++i) {
-                    if (flag[i]) {
-                        if (seen == target) { s_root = parent[i]; break; }
-                        ++seen;
+                for (int r = lo; r < hi; ++r) {
+                    uint32_t v = qrow[r];
+                    const int c = __popc(v);
+                    if (target < seen + c) {
+                        for (int m = target - seen; m > 0; --m) v &= v - 1u;
+                        s_root = parent[L * r + __ffs(v) - 1];
+                        break;
                     }
+                    seen += c;
                 }
             }
         }
@@ -250,54 +329,32 @@ __global__ void __launch_bounds__(512, 4) cluster_kernel(ClusterArgs a) {
     }
     if ((tid & 31) == 0) { s_top[0][tid >> 5] = t1; s_top[1][tid >> 5] = t2; }
     __syncthreads();
-    // energies of both clones (Eq. (1)) over the forward bonds of every
-    // 4-site word: exact FP32 pairs per thread, then the sum over threads
+    // energies (Eq. (1)).  The move conserves H_a + H_b exactly: a bond
+    // between a flipped and an unflipped cluster joins sites of opposite q,
+    // where the two clones' terms J s_i s_j cancel, and the bonds inside a
+    // flipped cluster do not change.  On the coupling grid (every thread's
+    // FP32 pair sum a multiple of 2^-18) only H_a is recomputed, summed
+    // exactly in integers, and H_b = (H_a + H_b before) - H_a after, exact in
+    // FP64 on the grid; the energies before are those of the resident spins
+    // (every entry point that changes spins recomputes them).  Off the grid
+    // both are recomputed and reduced in FP64.
     const float *J = b.J + (size_t)s * 3 * V;
-    float ha = 0.f, la_ = 0.f, hb = 0.f, lb_ = 0.f;
-    for (int w = tid; w < LW; w += T) {
-        const int c = w / (Gm::ROWS * W);
-        const int g = w - c * Gm::ROWS * W;
-        const GroupGeo q = group_geo<L>(g, c);
-        const int j = g % W;
-        const uint32_t X = 0x3F3F3F3Fu;
-        const uint32_t oA = sa[q.own], oB = sb[q.own];
-        const uint32_t xA = q.par ? __byte_perm(sa[q.wA], sa[q.wB], q.selx) : sa[q.xa];
-        const uint32_t xB = q.par ? __byte_perm(sb[q.wA], sb[q.wB], q.selx) : sb[q.xa];
-        // bytes 0x3F where s_i s_{i+mu} = +1, 0xBF where -1
-        const uint32_t pxA = oA ^ xA ^ X, pyA = oA ^ sa[q.yp] ^ X, pzA = oA ^ sa[q.zp] ^ X;
-        const uint32_t pxB = oB ^ xB ^ X, pyB = oB ^ sb[q.yp] ^ X, pzB = oB ^ sb[q.zp] ^ X;
-#pragma unroll
-        for (int kk = 0; kk < 4; ++kk) {
-            if (!Gm::FULL && 4 * j + kk >= Lh) continue;
-            const int i = site_of_word<L>(w, kk);
-            const float Jx = J[i], Jy = J[V + i], Jz = J[2 * V + i];
-            two_sum_acc(ha, la_, Jx * spinf(pxA, kk));
-            two_sum_acc(ha, la_, Jy * spinf(pyA, kk));
-            two_sum_acc(ha, la_, Jz * spinf(pzA, kk));
-            two_sum_acc(hb, lb_, Jx * spinf(pxB, kk));
-            two_sum_acc(hb, lb_, Jy * spinf(pyB, kk));
-            two_sum_acc(hb, lb_, Jz * spinf(pzB, kk));
-        }
-    }
-    // When every thread's pair sums lie on the 2^-18 grid (couplings on the
-    // grid), the sum over threads runs exactly in integers; otherwise in FP64.
-    const float xa = ha * 262144.f, xla = la_ * 262144.f, xb = hb * 262144.f, xlb = lb_ * 262144.f;
-    const bool ig = xa == rintf(xa) && xla == rintf(xla) && xb == rintf(xb) && xlb == rintf(xlb) &&
-                    fabsf(xa) < 536870912.f && fabsf(xb) < 536870912.f && fabsf(xla) < 65536.f &&
-                    fabsf(xlb) < 65536.f;
+    float ha = 0.f, la_ = 0.f;
+    clone_energy_pairs<L>(sa, J, tid, T, ha, la_);
+    const float xa = ha * 262144.f, xla = la_ * 262144.f;
+    const bool ig = xa == rintf(xa) && xla == rintf(xla) && fabsf(xa) < 536870912.f && fabsf(xla) < 65536.f;
     const bool exact_E = __syncthreads_and(ig) != 0;
     if (exact_E) {
         const int va = __float2int_rn(xa) + __float2int_rn(xla);
-        const int vb = __float2int_rn(xb) + __float2int_rn(xlb);
         // split so that the 32-lane sums cannot overflow
-        const int ah = __reduce_add_sync(0xffffffffu, va >> 12), bh = __reduce_add_sync(0xffffffffu, vb >> 12);
+        const int ah = __reduce_add_sync(0xffffffffu, va >> 12);
         const unsigned al = __reduce_add_sync(0xffffffffu, (unsigned)(va & 0xFFF));
-        const unsigned bl = __reduce_add_sync(0xffffffffu, (unsigned)(vb & 0xFFF));
-        if ((tid & 31) == 0) {
-            atomicAdd(&s_Ei[0], (unsigned long long)((long long)ah * 4096 + (long long)al));
-            atomicAdd(&s_Ei[1], (unsigned long long)((long long)bh * 4096 + (long long)bl));
-        }
+        if ((tid & 31) == 0) atomicAdd(&s_Ei[0], (unsigned long long)((long long)ah * 4096 + (long long)al));
     } else {
+        float hb = 0.f, lb_ = 0.f;
+        ha = 0.f;
+        la_ = 0.f;
+        clone_energy_pairs<L>(sa, J, tid, T, ha, la_, sb, &hb, &lb_);
         double ea = (double)ha + (double)la_, eb = (double)hb + (double)lb_;
         for (int o = 16; o > 0; o >>= 1) {
             ea += __shfl_xor_sync(0xffffffffu, ea, o);
@@ -311,8 +368,15 @@ __global__ void __launch_bounds__(512, 4) cluster_kernel(ClusterArgs a) {
         reinterpret_cast<uint4 *>(gb_ptr)[i] = reinterpret_cast<const uint4 *>(sb)[i];
     }
     if (tid == 0) {
-        b.E[(size_t)s * b.NLAT + la] = exact_E ? (double)(long long)s_Ei[0] * (-1.0 / 262144.0) : -s_E[0];
-        b.E[(size_t)s * b.NLAT + lb] = exact_E ? (double)(long long)s_Ei[1] * (-1.0 / 262144.0) : -s_E[1];
+        double *E = b.E + (size_t)s * b.NLAT;
+        if (exact_E) {
+            const double ea = (double)(long long)s_Ei[0] * (-1.0 / 262144.0);
+            E[lb] = (E[la] + E[lb]) - ea;
+            E[la] = ea;
+        } else {
+            E[la] = -s_E[0];
+            E[lb] = -s_E[1];
+        }
         int a1 = 0, a2 = 0;
         for (int w = 0; w < (T + 31) / 32; ++w) {
             const int u1 = s_top[0][w], u2 = s_top[1][w];
@@ -329,7 +393,8 @@ __global__ void __launch_bounds__(512, 4) cluster_kernel(ClusterArgs a) {
 template <int L>
 size_t cluster_smem(void) {
     using Gm = Geom<L>;
-    return (size_t)8 * Gm::V + (size_t)8 * Gm::LAT_WORDS + (size_t)Gm::V + 16;
+    return (size_t)8 * Gm::V + (size_t)8 * Gm::LAT_WORDS + (size_t)((Gm::V + 3) & ~3) +
+           (size_t)4 * L * L + 16;
 }
 
 template <int L>
