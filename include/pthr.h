@@ -97,12 +97,17 @@ enum { PTHR_OBS_MEASURE = 1, PTHR_OBS_READ_HOST = 2, PTHR_OBS_READ_DEVICE = 4, P
  *                                   sum over pairs of q^2 between the clone of
  *                                   group 2p at T_0 and the clone of group 2p+1
  *                                   at T_k (Sec. 5, chaotic parameter)
+ *  TABLES                           read-only, written at creation: double
+ *                                   T_k [n_temps], 1/T_k [n_temps],
+ *                                   (V-2n)/V [V+1], (3V-2n)/(3V) [3V+1], then
+ *                                   float -2 log2(e)/T_k [n_temps]; each value
+ *                                   one IEEE-rounded division
  */
 enum {
     PTHR_BUF_J = 0, PTHR_BUF_SPINS, PTHR_BUF_ENERGY, PTHR_BUF_PERM, PTHR_BUF_AGE,
     PTHR_BUF_RT, PTHR_BUF_TRIPS, PTHR_BUF_PTACC, PTHR_BUF_FLIPS, PTHR_BUF_OBS,
     PTHR_BUF_EMCS, PTHR_BUF_SEEDS, PTHR_BUF_ACTIVE, PTHR_BUF_STATUS, PTHR_BUF_CSTAT,
-    PTHR_BUF_CHAOS, PTHR_NBUF
+    PTHR_BUF_CHAOS, PTHR_BUF_TABLES, PTHR_NBUF
 };
 
 typedef struct {

@@ -22,7 +22,7 @@ OBS_MEASURE, OBS_READ_HOST, OBS_READ_DEVICE, OBS_RESET, OBS_CHAOS = 1, 2, 4, 8, 
 NOBS = 8
 MAX_L = 24
 (BUF_J, BUF_SPINS, BUF_ENERGY, BUF_PERM, BUF_AGE, BUF_RT, BUF_TRIPS, BUF_PTACC, BUF_FLIPS,
- BUF_OBS, BUF_EMCS, BUF_SEEDS, BUF_ACTIVE, BUF_STATUS, BUF_CSTAT, BUF_CHAOS, NBUF) = range(17)
+ BUF_OBS, BUF_EMCS, BUF_SEEDS, BUF_ACTIVE, BUF_STATUS, BUF_CSTAT, BUF_CHAOS, BUF_TABLES, NBUF) = range(18)
 
 # every exported entry point of include/pthr.h
 EXPORTS = ("pthr_required_bytes", "pthr_buffer_info", "pthr_lattice_bytes", "pthr_create_batch",

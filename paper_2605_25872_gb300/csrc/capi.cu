@@ -5,6 +5,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <vector>
 #include <thread>
 
 #include "kernels.cuh"
@@ -123,6 +124,7 @@ Layout make_layout(const pthr_config *c) {
     l.len[PTHR_BUF_STATUS] = 4 * sizeof(uint32_t);
     l.len[PTHR_BUF_CSTAT] = S * NP * NT * 4 * sizeof(long long);
     l.len[PTHR_BUF_CHAOS] = S * NT * 2 * sizeof(double);
+    l.len[PTHR_BUF_TABLES] = (2 * NT + 4 * V + 2) * sizeof(double) + NT * sizeof(float);
     size_t o = 0;
     for (int i = 0; i < PTHR_NBUF; ++i) {
         l.off[i] = o;
@@ -141,7 +143,7 @@ int default_k(const pthr_config *c, int total_entries) {
     const size_t lb = (size_t)lattice_words(c->L) * 4;
     const size_t budget = 220 * 1024;
     long k = (long)((budget - 12 * lb) / lb);
-    if (c->L == 16) k = 16;
+    if (c->L >= 12 && k > 16) k = 16;   // from L = 12 up; two blocks per SM at L = 12
     if (k > sweep_max_k()) k = sweep_max_k();
     if (k < 1) k = 1;
     if (k > total_entries) k = total_entries;
@@ -335,6 +337,13 @@ PTHR_API pthr_status pthr_create_batch(const pthr_config *cfg, void *device_work
     d.status = (uint32_t *)(base + l.off[PTHR_BUF_STATUS]);
     d.cstat = (long long *)(base + l.off[PTHR_BUF_CSTAT]);
     d.chaos = (double *)(base + l.off[PTHR_BUF_CHAOS]);
+    double *tab = (double *)(base + l.off[PTHR_BUF_TABLES]);
+    const int NTt = cfg->n_temps, Vt = cfg->L * cfg->L * cfg->L;
+    d.tabT = tab;
+    d.tabBeta = tab + NTt;
+    d.tabQ = tab + 2 * NTt;
+    d.tabQl = tab + 2 * NTt + Vt + 1;
+    d.tabTb = (const float *)(tab + 2 * NTt + 4 * Vt + 2);
     d.S = cfg->n_samples;
     d.L = cfg->L;
     d.NT = cfg->n_temps;
@@ -359,6 +368,27 @@ PTHR_API pthr_status pthr_create_batch(const pthr_config *cfg, void *device_work
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);   // hs is pageable and freed below
     delete[] hs;
     if (e == cudaSuccess) e = cudaMemsetAsync(d.status, 0, 16, b->stream);
+    if (e == cudaSuccess) {
+        // tables: one IEEE-rounded division each, the same bits as the
+        // per-use divisions they replace
+        std::vector<unsigned char> ht(l.len[PTHR_BUF_TABLES]);
+        double *T = (double *)ht.data();
+        double *beta = T + NTt, *q = T + 2 * NTt, *ql = q + Vt + 1;
+        float *tb = (float *)(ql + 3 * Vt + 1);
+        for (int k = 0; k < NTt; ++k) {
+            T[k] = host_temperature(cfg, k);
+            volatile double one = 1.0, m2l2e = -2.0 * 1.4426950408889634073599;
+            beta[k] = one / T[k];
+            tb[k] = (float)(m2l2e / T[k]);
+        }
+        for (int n = 0; n <= Vt; ++n) { volatile double num = (double)(Vt - 2 * n); q[n] = num / (double)Vt; }
+        for (int n = 0; n <= 3 * Vt; ++n) {
+            volatile double num = (double)(3 * Vt - 2 * n), den = 3.0 * (double)Vt;
+            ql[n] = num / den;
+        }
+        e = cudaMemcpyAsync(tab, ht.data(), ht.size(), cudaMemcpyHostToDevice, b->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);   // ht is freed below
+    }
     if (e != cudaSuccess) { pthr_status r = cuda_fail(nullptr, e, "create"); delete b; return r; }
     if (couplings) {
         e = cudaMemcpyAsync(d.J, couplings, l.len[PTHR_BUF_J], cudaMemcpyDefault, b->stream);

@@ -58,6 +58,28 @@ __device__ __forceinline__ uint32_t spread_bits(uint32_t v) {
     return v;
 }
 
+// bit 2m of v -> bit m
+__device__ __forceinline__ uint32_t compact_bits(uint32_t v) {
+    v &= 0x55555555u;
+    v = (v | (v >> 1)) & 0x33333333u;
+    v = (v | (v >> 2)) & 0x0F0F0F0Fu;
+    v = (v | (v >> 4)) & 0x00FF00FFu;
+    v = (v | (v >> 8)) & 0x0000FFFFu;
+    return v;
+}
+
+// bit 7 of the four bytes of w (the sign of a packed spin, or where two
+// packed words differ) as the low four bits; a multiply gathers them
+__device__ __forceinline__ uint32_t sign_nibble(uint32_t w) {
+    return ((w & 0x80808080u) * 0x00204081u) >> 28;
+}
+
+// L-bit row rotated so that bit x holds bit (x + 1) mod L
+template <int L>
+__device__ __forceinline__ uint32_t rot_next(uint32_t v) {
+    return (v >> 1) | ((v & 1u) << (L - 1));
+}
+
 // natural site index of byte kk of packed word w
 template <int L>
 __device__ __forceinline__ int site_of_word(int w, int kk) {
@@ -130,7 +152,9 @@ __global__ void __launch_bounds__(512, 4) cluster_kernel(ClusterArgs a) {
     uint32_t *sa = reinterpret_cast<uint32_t *>(cnt + V);              // [LW]
     uint32_t *sb = sa + LW;                                            // [LW]
     unsigned char *flag = reinterpret_cast<unsigned char *>(sb + LW);  // [V] sign of each root
-    uint32_t *qrow = reinterpret_cast<uint32_t *>(flag + ((V + 3) & ~3));  // [L*L] q bits per x row
+    uint32_t *qrow = reinterpret_cast<uint32_t *>(flag + ((V + 3) & ~3));  // [L*L] q bits per x row,
+                                                                           // later the flip bits
+    uint32_t *arow = qrow + L * L;                                     // [L*L] clone a: 1 = spin -1
     __shared__ int s_ok;
     __shared__ int s_nneg, s_root, s_nclus, s_nflip;
     __shared__ int s_top[2][32];
@@ -171,20 +195,22 @@ __global__ void __launch_bounds__(512, 4) cluster_kernel(ClusterArgs a) {
     constexpr uint32_t M = L == 32 ? 0xffffffffu : ((1u << L) - 1u);
     for (int r = tid; r < L * L; r += T) {
         const int y = r % L, z = r / L;
-        uint32_t bits[2];
+        uint32_t bits[2], abits[2];
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
-            uint32_t acc = 0;
+            uint32_t acc = 0, aacc = 0;
 #pragma unroll
             for (int j = 0; j < W; ++j) {
                 const int w = (c * Gm::ROWS + r) * W + j;
-                const uint32_t qw = (sa[w] ^ sb[w]) & 0x80808080u;
-                acc |= ((qw * 0x00204081u) >> 28) << (4 * j);
+                acc |= sign_nibble(sa[w] ^ sb[w]) << (4 * j);
+                aacc |= sign_nibble(sa[w]) << (4 * j);
             }
             bits[c] = acc & ((1u << Lh) - 1u);
+            abits[c] = aacc & ((1u << Lh) - 1u);
         }
         const int p0 = (y + z) & 1;
         qrow[r] = (spread_bits(bits[0]) << p0) | (spread_bits(bits[1]) << (p0 ^ 1));
+        arow[r] = (spread_bits(abits[0]) << p0) | (spread_bits(abits[1]) << (p0 ^ 1));
     }
     for (int i = tid; i < V; i += T) cnt[i] = 0;
     __syncthreads();
@@ -295,20 +321,16 @@ __global__ void __launch_bounds__(512, 4) cluster_kernel(ClusterArgs a) {
             if (parent[i] == i) flag[i] = (unsigned char)(i == root);
         __syncthreads();
     }
-    // flip both clones on the selected clusters, one 4-site word at a time
+    // flip bits of every natural x row (bit x set iff the cluster of site
+    // x + L r is flipped); the q rows are no longer needed
+    uint32_t *frow = qrow;
     int nflip = 0;
-    for (int w = tid; w < LW; w += T) {
-        const int j = (w % (Gm::ROWS * W)) % W;
-        uint32_t m = 0u;
+    for (int r = tid; r < L * L; r += T) {
+        uint32_t f = 0u;
 #pragma unroll
-        for (int kk = 0; kk < 4; ++kk) {
-            if (!Gm::FULL && 4 * j + kk >= Lh) continue;
-            const int i = site_of_word<L>(w, kk);
-            if (flag[parent[i]]) m |= 0x80u << (8 * kk);
-        }
-        sa[w] ^= m;
-        sb[w] ^= m;
-        nflip += __popc(m);
+        for (int x = 0; x < L; ++x) f |= (uint32_t)flag[parent[L * r + x]] << x;
+        frow[r] = f;
+        nflip += __popc(f);
     }
     // statistics: number of clusters, two largest sizes
     int nroots = 0, t1 = 0, t2 = 0;
@@ -329,18 +351,46 @@ __global__ void __launch_bounds__(512, 4) cluster_kernel(ClusterArgs a) {
     }
     if ((tid & 31) == 0) { s_top[0][tid >> 5] = t1; s_top[1][tid >> 5] = t2; }
     __syncthreads();
-    // energies (Eq. (1)).  The move conserves H_a + H_b exactly: a bond
-    // between a flipped and an unflipped cluster joins sites of opposite q,
-    // where the two clones' terms J s_i s_j cancel, and the bonds inside a
-    // flipped cluster do not change.  On the coupling grid (every thread's
-    // FP32 pair sum a multiple of 2^-18) only H_a is recomputed, summed
-    // exactly in integers, and H_b = (H_a + H_b before) - H_a after, exact in
-    // FP64 on the grid; the energies before are those of the resident spins
-    // (every entry point that changes spins recomputes them).  Off the grid
-    // both are recomputed and reduced in FP64.
+    // flip both clones word by word: the colour-c bits of the row mask,
+    // compacted, give the word's four flip bits
+    for (int w = tid; w < LW; w += T) {
+        const int c = w / (Gm::ROWS * W);
+        const int g = w - c * Gm::ROWS * W;
+        const int r = g / W, j = g - r * W;
+        const int y = r % L, z = r / L;
+        const uint32_t nib = (compact_bits(frow[r] >> ((c + y + z) & 1)) >> (4 * j)) & 0xFu;
+        const uint32_t m = ((nib * 0x00204081u) & 0x01010101u) << 7;
+        sa[w] ^= m;
+        sb[w] ^= m;
+    }
+    // energies (Eq. (1)).  Only bonds with exactly one flipped end change:
+    // for them s'_i s'_j = -s_i s_j, so Delta H_a = sum of 2 J s_i s_j (old
+    // spins of clone a).  Such a bond joins sites of opposite q, where the two
+    // clones' terms cancel, so H_a + H_b is conserved and Delta H_b =
+    // -Delta H_a.  On the coupling grid (every thread's FP32 pair sum a
+    // multiple of 2^-18) Delta H_a is summed exactly in integers and both
+    // energies are updated exactly in FP64; the energies before are those of
+    // the resident spins (every entry point that changes spins recomputes
+    // them).  Off the grid both energies are recomputed and reduced in FP64.
     const float *J = b.J + (size_t)s * 3 * V;
     float ha = 0.f, la_ = 0.f;
-    clone_energy_pairs<L>(sa, J, tid, T, ha, la_);
+    for (int r = tid; r < L * L; r += T) {
+        const int y = r % L, z = r / L;
+        const int ry = ((y + 1) % L) + L * z, rz = y + L * ((z + 1) % L);
+        const uint32_t f = frow[r], av = arow[r];
+        const uint32_t cut[3] = {f ^ rot_next<L>(f), f ^ frow[ry], f ^ frow[rz]};
+        const uint32_t neg[3] = {av ^ rot_next<L>(av), av ^ arow[ry], av ^ arow[rz]};
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            uint32_t cb = cut[d];
+            while (cb) {
+                const int x = __ffs(cb) - 1;
+                cb &= cb - 1u;
+                const float t = 2.f * J[d * V + L * r + x];
+                two_sum_acc(ha, la_, ((neg[d] >> x) & 1u) ? -t : t);
+            }
+        }
+    }
     const float xa = ha * 262144.f, xla = la_ * 262144.f;
     const bool ig = xa == rintf(xa) && xla == rintf(xla) && fabsf(xa) < 536870912.f && fabsf(xla) < 65536.f;
     const bool exact_E = __syncthreads_and(ig) != 0;
@@ -370,9 +420,9 @@ __global__ void __launch_bounds__(512, 4) cluster_kernel(ClusterArgs a) {
     if (tid == 0) {
         double *E = b.E + (size_t)s * b.NLAT;
         if (exact_E) {
-            const double ea = (double)(long long)s_Ei[0] * (-1.0 / 262144.0);
-            E[lb] = (E[la] + E[lb]) - ea;
-            E[la] = ea;
+            const double dH = (double)(long long)s_Ei[0] * (1.0 / 262144.0);
+            E[la] = E[la] + dH;
+            E[lb] = E[lb] - dH;
         } else {
             E[la] = -s_E[0];
             E[lb] = -s_E[1];
@@ -394,7 +444,7 @@ template <int L>
 size_t cluster_smem(void) {
     using Gm = Geom<L>;
     return (size_t)8 * Gm::V + (size_t)8 * Gm::LAT_WORDS + (size_t)((Gm::V + 3) & ~3) +
-           (size_t)4 * L * L + 16;
+           (size_t)8 * L * L + 16;
 }
 
 template <int L>

@@ -36,8 +36,7 @@ __global__ void swap_kernel(Batch b, int flags, int first) {
             long long *acc = b.ptacc + ((size_t)s * b.NR + g) * b.NT;
             for (int ph = 0; ph < 2; ++ph) {
                 for (int k = ph + 2 * lane; k + 1 < b.NT; k += 64) {
-                    const double bk = __ddiv_rn(1.0, temperature(b, k));
-                    const double bk1 = __ddiv_rn(1.0, temperature(b, k + 1));
+                    const double bk = b.tabBeta[k], bk1 = b.tabBeta[k + 1];
                     const double delta = __dmul_rn(__dsub_rn(bk, bk1), __dsub_rn(Ep[k], Ep[k + 1]));
                     bool accept = delta >= 0.0;
                     if (!accept) {
@@ -149,20 +148,23 @@ __global__ void measure_kernel(Batch b, int first, int chaos) {
     if (wid != 0) return;
     // per-group energy density on lane g, per-pair overlaps on lane P
     double e = 0.0, q = 0.0, ql = 0.0, S = 0.0, qc = 0.0;
+    // e = H / V (exact scaling when V is a power of two); q, q_l and T_k
+    // come from the creation-time tables of the same divisions
     if (lane < b.NR) {
         const int lat = lane * b.NSLOT + perm[lane * b.NSLOT + k];
-        e = __ddiv_rn(b.E[(size_t)s * b.NLAT + lat], (double)V);
+        const double H = b.E[(size_t)s * b.NLAT + lat];
+        e = ((V & (V - 1)) == 0) ? __dmul_rn(H, 1.0 / (double)V) : __ddiv_rn(H, (double)V);
     }
     if (lane < b.NPAIR) {
         int tn = 0, td = 0, tc = 0;
         for (int w = 0; w < T / 32; ++w) { tn += s_cnt[0][lane][w]; td += s_cnt[1][lane][w]; tc += s_cnt[2][lane][w]; }
-        const double Tk = temperature(b, k);
+        const double Tk = b.tabT[k];
         const int la = 2 * lane * b.NSLOT + perm[2 * lane * b.NSLOT + k];
-        q = __ddiv_rn((double)(V - 2 * tn), (double)V);
-        ql = __ddiv_rn((double)(3 * V - 2 * td), 3.0 * (double)V);
+        q = b.tabQ[tn];
+        ql = b.tabQl[td];
         const double Ha = b.E[(size_t)s * b.NLAT + la];
         S = __dadd_rn(__ddiv_rn(Ha, 3.0 * (double)V), __ddiv_rn(__dsub_rn(1.0, ql), Tk));
-        qc = __ddiv_rn((double)(V - 2 * tc), (double)V);
+        qc = b.tabQ[tc];
     }
     double *o = b.obs + ((size_t)s * b.NT + k) * PTHR_NOBS;
     double se = 0.0, se2 = 0.0;

@@ -69,6 +69,11 @@ struct Batch {
     uint32_t *status;         // [4]
     long long *cstat;         // [S][NPAIR][NT][4]
     double *chaos;            // [S][NT][2]
+    const double *tabT;       // [NT]    T_k
+    const double *tabBeta;    // [NT]    1 / T_k
+    const double *tabQ;       // [V+1]   (V - 2n) / V
+    const double *tabQl;      // [3V+1]  (3V - 2n) / (3V)
+    const float *tabTb;       // [NT]    (float)(-2 log2(e) / T_k)
     int S, L, NT, NR, NRES, NSLOT, NLAT, NPAIR, lat_words;
     int rule, cluster_mode, acu_interval, n_acu;
     double t_min, t_max;

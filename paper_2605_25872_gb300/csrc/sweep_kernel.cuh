@@ -180,8 +180,29 @@ __device__ __forceinline__ void segment_sum(long long &w, unsigned &f, int lane,
     }
 }
 
+// Groups per lattice lane for size L: all G groups of a colour when G <= 512,
+// else the largest proper divisor of G that is at most 512 (the host's block
+// shape follows the same rule).
+constexpr int groups_per_lane(int G) {
+    if (G <= 512) return G;
+    for (int d = 2; d <= G; ++d)
+        if (G % d == 0 && G / d <= 512) return G / d;
+    return 1;
+}
+// Largest block of size L (whole lattice lanes, at most 512 threads), and the
+// blocks per SM to keep registers for: for the Metropolis rule two when two
+// such blocks fit at 112 registers a thread (L = 12: 288 threads).
+template <int L, int RULE>
+struct SweepBounds {
+    static constexpr int Gt = groups_per_lane(Geom<L>::G);
+    static constexpr int threads = Gt * (512 / Gt);
+    static constexpr int min_blocks =
+        (RULE == PTHR_METROPOLIS && 65536 / (threads * 112) >= 2) ? 2 : 1;
+};
+
 template <int L, int RULE, int KT>
-__global__ void __launch_bounds__(512) sweep_kernel(SweepArgs a) {
+__global__ void __launch_bounds__(SweepBounds<L, RULE>::threads, SweepBounds<L, RULE>::min_blocks)
+sweep_kernel(SweepArgs a) {
     using Gm = Geom<L>;
     constexpr int W = Gm::W, ROWS = Gm::ROWS, Lh = Gm::Lh, G = Gm::G;
     constexpr int LW = Gm::LAT_WORDS, LB = Gm::LAT_BYTES;
@@ -231,9 +252,8 @@ __global__ void __launch_bounds__(512) sweep_kernel(SweepArgs a) {
         const int g = e / per, pos = kind ? b.NT + (e % per) : (e % per);
         const int clone = b.perm[((size_t)s * b.NR + g) * b.NSLOT + pos];
         s_lat[tid] = g * b.NSLOT + clone;
-        const double T_k = temperature(b, kind ? b.NT - 1 : pos);
         // -2 beta log2(e): exp(-beta dE) = 2^(tb t) with dE = 2 t
-        s_tb[tid] = (float)(-2.0 * 1.4426950408889634073599 / T_k);
+        s_tb[tid] = b.tabTb[kind ? b.NT - 1 : pos];
         s_flips[tid] = 0u;
         s_E[tid] = 0.0;
         s_Ei[tid] = 0ull;
