@@ -358,12 +358,22 @@ sweep_kernel(SweepArgs a) {
                     Jc[kk][4] = Js[2 * LB + so];
                     Jc[kk][5] = Js[2 * LB + 4 * ((cc * ROWS + rzm) * W) + m];
                 }
-                // the same couplings as packed pairs (sites 0,1 and 2,3)
+                // the same couplings as packed pairs (sites 0,1 and 2,3); the x
+                // pair is ordered as (aligned word xa, shifted word xs), so the
+                // lattice loop needs no select on the row parity
                 f2 Jp[2][6];
 #pragma unroll
                 for (int n = 0; n < 6; ++n) {
                     Jp[0][n] = pack2(Jc[0][n], Jc[1][n]);
                     Jp[1][n] = pack2(Jc[2][n], Jc[3][n]);
+                }
+                if (q.par) {
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const f2 t = Jp[h][0];
+                        Jp[h][0] = Jp[h][1];
+                        Jp[h][1] = t;
+                    }
                 }
                 // flip-mask bits of the real sites of this group
                 uint32_t vmask = 0x80808080u;
@@ -379,7 +389,6 @@ sweep_kernel(SweepArgs a) {
                     const uint32_t own = S[q.own];
                     const uint32_t xa = S[q.xa];
                     const uint32_t xs = __byte_perm(S[q.wA], S[q.wB], q.selx);
-                    const uint32_t wxp = q.par ? xs : xa, wxm = q.par ? xa : xs;
                     const uint32_t wyp = S[q.yp], wym = S[q.ym], wzp = S[q.zp], wzm = S[q.zm];
                     const u4 rnd = philox10_rk((uint32_t)g, (uint32_t)s_lat[k], emcs, c3, rk0, rk1);
                     const uint32_t rw[4] = {rnd.x, rnd.y, rnd.z, rnd.w};
@@ -388,7 +397,7 @@ sweep_kernel(SweepArgs a) {
                     if (RULE == PTHR_METROPOLIS) {
                         // bytes 0x3F where s_i s_j = +1, 0xBF where -1
                         const uint32_t X = 0x3F3F3F3Fu;
-                        const uint32_t pxp = own ^ wxp ^ X, pxm = own ^ wxm ^ X;
+                        const uint32_t pxa = own ^ xa ^ X, pxs = own ^ xs ^ X;
                         const uint32_t pyp = own ^ wyp ^ X, pym = own ^ wym ^ X;
                         const uint32_t pzp = own ^ wzp ^ X, pzm = own ^ wzm ^ X;
                         float dv[4];
@@ -397,8 +406,8 @@ sweep_kernel(SweepArgs a) {
 #pragma unroll
                         for (int h = 0; h < 2; ++h) {
                             // t = sum_j J_ij s_i s_j for sites 2h, 2h+1 (packed)
-                            f2 tt = mul2(Jp[h][0], spin_pair(pxp, h));
-                            tt = fma2(Jp[h][1], spin_pair(pxm, h), tt);
+                            f2 tt = mul2(Jp[h][0], spin_pair(pxa, h));
+                            tt = fma2(Jp[h][1], spin_pair(pxs, h), tt);
                             tt = fma2(Jp[h][2], spin_pair(pyp, h), tt);
                             tt = fma2(Jp[h][3], spin_pair(pym, h), tt);
                             tt = fma2(Jp[h][4], spin_pair(pzp, h), tt);
@@ -417,6 +426,7 @@ sweep_kernel(SweepArgs a) {
                         fm = __byte_perm(lo, hi, 0x7610u) & vmask;
                     } else {
                         fm = 0u;
+                        const uint32_t wxp = q.par ? xs : xa, wxm = q.par ? xa : xs;
 #pragma unroll
                         for (int kk = 0; kk < 4; ++kk) {
                             const float si = spinf(own, kk);

@@ -220,6 +220,40 @@ def test_cluster_move_parity(mode, L):
         mir.swap(pt=False, er=False)
 
 
+@pytest.mark.parametrize("kind", ["offgrid", "wide"])
+def test_cluster_move_energies_outside_the_exact_grid(kind):
+    """Cluster moves with couplings off the 2^-18 grid (both energies are
+    recomputed and reduced in FP64: within 1e-9 of the oracle) and with on-grid
+    couplings up to |J| = 32 (the sweep's energies take the FP64 path, the
+    cluster step's cut-bond update stays exact: equal to the oracle)."""
+    L = 8
+    cfg = BatchConfig(L=L, n_samples=3, n_temps=8, n_replicas=4, n_res=2, cluster="acu")
+    seeds = W.sample_seeds(W.SEED_BASE + 71, cfg.n_samples)
+    if kind == "offgrid":
+        J = W.gaussian_couplings(L, cfg.n_samples, 71, on_grid=False)
+    else:
+        J = (W.gaussian_couplings(L, cfg.n_samples, 71, on_grid=True) * 4.0).astype(np.float32)
+    gpu = Batch(cfg, couplings=J, seeds=seeds)
+    mir = Mirror(cfg, J, seeds)
+    spins = W.random_spins((cfg.n_samples, cfg.n_lat, cfg.V), 2071)
+    gpu.import_spins(torch.from_numpy(spins))
+    for s, smp in enumerate(mir.samples):
+        smp.spins[:] = spins[s]
+        for lat in range(cfg.n_lat):
+            smp.E_lat[lat] = O.energy(L, smp.J, smp.spins[lat])
+    for rep in range(3):
+        gpu.houdayer()
+        mir.houdayer()
+        np.testing.assert_array_equal(gpu_spins(gpu), mir.spins())
+        Eg, Eo = gpu.energies.cpu().numpy(), mir.energies()
+        if kind == "offgrid":
+            np.testing.assert_allclose(Eg, Eo, rtol=1e-9, atol=1e-9)
+        else:
+            np.testing.assert_array_equal(Eg, Eo)
+        gpu.swap(pt=False, er=False)
+        mir.swap(pt=False, er=False)
+
+
 # ----------------------------------------------------------------------------- a7/a8/a9 and full EMCS
 
 def run_emcs_parity(cfg, n_emcs, seed):
