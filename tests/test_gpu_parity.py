@@ -96,6 +96,31 @@ def test_couplings_from_seed_match_oracle():
     assert np.all(np.abs(Jg.astype(np.float64) - Jo)[diff] <= 2.0 ** -18)
 
 
+@pytest.mark.parametrize("L,n_temps,t_min,t_max", [(6, 13, 0.2, 1.6), (10, 7, 0.35, 2.0)])
+def test_creation_tables_match_their_definitions(L, n_temps, t_min, t_max):
+    """The creation-time tables equal, bit for bit, the oracle's temperature
+    grid and 1/T_k, the IEEE quotients (V - 2n)/V and (3V - 2n)/(3V), and the
+    FP32 sweep factor -2 log2(e) / T_k."""
+    from paper_2605_25872_gb300 import _lib, buffer_info
+    cfg = BatchConfig(L=L, n_samples=1, n_temps=n_temps, n_replicas=2, n_res=1, t_min=t_min,
+                      t_max=t_max)
+    gpu = Batch(cfg)
+    off, n = buffer_info(cfg, _lib.BUF_TABLES)
+    raw = gpu.ws[off:off + n].cpu().numpy()
+    V, NT = cfg.V, n_temps
+    nd = 2 * NT + 4 * V + 2
+    d = raw[:8 * nd].view(np.float64)
+    tb = raw[8 * nd:8 * nd + 4 * NT].view(np.float32)
+    T, beta = O.temperatures(NT, t_min, t_max)
+    np.testing.assert_array_equal(d[:NT], T)
+    np.testing.assert_array_equal(d[NT:2 * NT], beta)
+    m = np.arange(V + 1, dtype=np.float64)
+    np.testing.assert_array_equal(d[2 * NT:2 * NT + V + 1], (V - 2 * m) / float(V))
+    m3 = np.arange(3 * V + 1, dtype=np.float64)
+    np.testing.assert_array_equal(d[2 * NT + V + 1:nd], (3 * V - 2 * m3) / (3.0 * V))
+    np.testing.assert_array_equal(tb, ((-2.0 * 1.4426950408889634073599) / T).astype(np.float32))
+
+
 @pytest.mark.parametrize("L", [2, 4, 6, 8, 10, 12, 16])
 def test_init_state_matches_oracle(L):
     cfg = BatchConfig(L=L, n_samples=3, n_temps=5, n_replicas=4, n_res=3)
