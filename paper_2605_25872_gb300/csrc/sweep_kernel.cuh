@@ -44,11 +44,11 @@ __device__ __forceinline__ void mul_wide(uint32_t a, uint32_t b, uint32_t &hi, u
 // In rounds 0-2 some products do not depend on the lattice: M1 * emcs is
 // fixed for the block, M0 * g for the group, and with the colour/sweep word
 // c3 the round-0 output word 2, then M1 times it and M0 times the round-1
-// output word 0, are fixed for a (group, colour, sweep).  SweepRng holds
-// those parts already combined with their round keys, so a lattice costs 16
-// wide multiplies and 18 XORs instead of 20 and 20.
+// output word 0, are fixed for a (group, colour, sweep); M0 times the
+// round-0 word 0 is fixed for a lattice.  SweepRng holds the group parts
+// already combined with their round keys, so a draw costs 15 wide
+// multiplies and 17 XORs instead of 20 and 20.
 struct SweepRng {
-    uint32_t x1;    // hi(M1 * emcs) ^ rk0[0]: XOR with the lattice id gives round-0 word 0
     uint32_t y2;    // lo(M0 * g) ^ rk1[1]
     uint32_t z3;    // lo(M1 * w2) ^ rk0[2], w2 = round-0 output word 2
     uint32_t w3;    // hi(M0 * v0) ^ rk1[2], v0 = round-1 output word 0
@@ -56,8 +56,9 @@ struct SweepRng {
 };
 
 // Parts fixed for a (group, colour, sweep): ahi, alo = M0 * g; elo =
-// lo(M1 * emcs); x1 as above; c3 = the counter's colour/sweep word.
-__device__ __forceinline__ SweepRng sweep_rng(uint32_t x1, uint32_t ahi, uint32_t alo, uint32_t elo,
+// lo(M1 * emcs); c3 = the counter's colour/sweep word.  (Round-0 word 0 is
+// hi(M1 * emcs) ^ rk0[0] ^ lat; the block prologue multiplies it per lattice.)
+__device__ __forceinline__ SweepRng sweep_rng(uint32_t ahi, uint32_t alo, uint32_t elo,
                                               uint32_t c3, const uint32_t (&rk0)[10],
                                               const uint32_t (&rk1)[10]) {
     const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
@@ -66,17 +67,17 @@ __device__ __forceinline__ SweepRng sweep_rng(uint32_t x1, uint32_t ahi, uint32_
     mul_wide(M1, w2, bhi, blo);
     const uint32_t v0 = bhi ^ elo ^ rk0[1];
     mul_wide(M0, v0, chi, clo);
-    return SweepRng{x1, alo ^ rk1[1], blo ^ rk0[2], chi ^ rk1[2], clo};
+    return SweepRng{alo ^ rk1[1], blo ^ rk0[2], chi ^ rk1[2], clo};
 }
 
-// Philox4x32-10 of (g, lat, emcs, c3) from the precomputed parts: rounds 1
-// and 2 need one wide multiply each, rounds 3-9 are computed in full.
-__device__ __forceinline__ u4 philox10_sweep(uint32_t lat, const SweepRng &p,
+// Philox4x32-10 of (g, lat, emcs, c3) from the precomputed parts; (ph, pl)
+// = M0 * (hi(M1 * emcs) ^ rk0[0] ^ lat), fixed per lattice for a launch.
+// Round 2 needs one wide multiply, rounds 3-9 are computed in full.
+__device__ __forceinline__ u4 philox10_sweep(uint32_t ph, uint32_t pl, const SweepRng &p,
                                              const uint32_t (&rk0)[10], const uint32_t (&rk1)[10]) {
     const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
     uint32_t hi, lo;
-    mul_wide(M0, p.x1 ^ lat, hi, lo);           // round 1, lattice-dependent half
-    const uint32_t a2 = hi ^ p.y2, a3 = lo;
+    const uint32_t a2 = ph ^ p.y2, a3 = pl;      // round 1
     mul_wide(M1, a2, hi, lo);                   // round 2, lattice-dependent half
     uint32_t c0 = hi ^ p.z3, c1 = lo, c2 = a3 ^ p.w3, c3 = p.clo;
 #pragma unroll
@@ -251,6 +252,7 @@ sweep_kernel(SweepArgs a) {
     __shared__ unsigned int s_flips[MAXK];
     __shared__ double s_E[MAXK];
     __shared__ unsigned long long s_Ei[MAXK];
+    __shared__ uint32_t s_rph[MAXK], s_rpl[MAXK];   // M0 * (round-0 word 0) per lattice
 
     const Batch &b = a.b;
     // ---- decode the task
@@ -295,6 +297,12 @@ sweep_kernel(SweepArgs a) {
         const int g = e / per, pos = kind ? b.NT + (e % per) : (e % per);
         const int clone = b.perm[((size_t)s * b.NR + g) * b.NSLOT + pos];
         s_lat[tid] = g * b.NSLOT + clone;
+        // round 1 of every sweep draw of this lattice starts from M0 times
+        // its round-0 word 0, which depends on the lattice and the block only
+        uint32_t ph, pl;
+        mul_wide(0xD2511F53u, rng_x1 ^ (uint32_t)(g * b.NSLOT + clone), ph, pl);
+        s_rph[tid] = ph;
+        s_rpl[tid] = pl;
         // -2 beta log2(e): exp(-beta dE) = 2^(tb t) with dE = 2 t
         s_tb[tid] = b.tabTb[kind ? b.NT - 1 : pos];
         s_flips[tid] = 0u;
@@ -383,7 +391,7 @@ sweep_kernel(SweepArgs a) {
                 const GroupGeo q = group_geo<L>(g, c);
                 uint32_t ahi, alo;
                 mul_wide(0xD2511F53u, (uint32_t)g, ahi, alo);
-                const SweepRng rng = sweep_rng(rng_x1, ahi, alo, rng_elo, c3, rk0, rk1);
+                const SweepRng rng = sweep_rng(ahi, alo, rng_elo, c3, rk0, rk1);
                 const int j = g % W;
                 const int cc = c ^ 1;
                 const int r = g / W;
@@ -436,7 +444,7 @@ sweep_kernel(SweepArgs a) {
                     const uint32_t xa = S[q.xa];
                     const uint32_t xs = __byte_perm(S[q.wA], S[q.wB], q.selx);
                     const uint32_t wyp = S[q.yp], wym = S[q.ym], wzp = S[q.zp], wzm = S[q.zm];
-                    const u4 rnd = philox10_sweep((uint32_t)s_lat[k], rng, rk0, rk1);
+                    const u4 rnd = philox10_sweep(s_rph[k], s_rpl[k], rng, rk0, rk1);
                     const uint32_t rw[4] = {rnd.x, rnd.y, rnd.z, rnd.w};
                     const float tb = s_tb[k];
                     uint32_t fm;
