@@ -248,11 +248,12 @@ sweep_kernel(SweepArgs a) {
     float *Js = reinterpret_cast<float *>(smem);                       // [3][LB]
     uint32_t *Ss = reinterpret_cast<uint32_t *>(smem + 12 * LB);       // [K][LW]
     __shared__ int s_lat[MAXK];
-    __shared__ float s_tb[MAXK];
     __shared__ unsigned int s_flips[MAXK];
     __shared__ double s_E[MAXK];
     __shared__ unsigned long long s_Ei[MAXK];
-    __shared__ uint32_t s_rph[MAXK], s_rpl[MAXK];   // M0 * (round-0 word 0) per lattice
+    // per lattice: M0 * (round-0 word 0) of its draws (hi, lo) and the
+    // exponent factor tb, read together with one 16-byte load
+    __shared__ uint4 s_lr[MAXK];
 
     const Batch &b = a.b;
     // ---- decode the task
@@ -301,10 +302,8 @@ sweep_kernel(SweepArgs a) {
         // its round-0 word 0, which depends on the lattice and the block only
         uint32_t ph, pl;
         mul_wide(0xD2511F53u, rng_x1 ^ (uint32_t)(g * b.NSLOT + clone), ph, pl);
-        s_rph[tid] = ph;
-        s_rpl[tid] = pl;
         // -2 beta log2(e): exp(-beta dE) = 2^(tb t) with dE = 2 t
-        s_tb[tid] = b.tabTb[kind ? b.NT - 1 : pos];
+        s_lr[tid] = make_uint4(ph, pl, __float_as_uint(b.tabTb[kind ? b.NT - 1 : pos]), 0u);
         s_flips[tid] = 0u;
         s_E[tid] = 0.0;
         s_Ei[tid] = 0ull;
@@ -444,9 +443,10 @@ sweep_kernel(SweepArgs a) {
                     const uint32_t xa = S[q.xa];
                     const uint32_t xs = __byte_perm(S[q.wA], S[q.wB], q.selx);
                     const uint32_t wyp = S[q.yp], wym = S[q.ym], wzp = S[q.zp], wzm = S[q.zm];
-                    const u4 rnd = philox10_sweep(s_rph[k], s_rpl[k], rng, rk0, rk1);
+                    const uint4 lr = s_lr[k];
+                    const u4 rnd = philox10_sweep(lr.x, lr.y, rng, rk0, rk1);
                     const uint32_t rw[4] = {rnd.x, rnd.y, rnd.z, rnd.w};
-                    const float tb = s_tb[k];
+                    const float tb = __uint_as_float(lr.z);
                     uint32_t fm;
                     if (RULE == PTHR_METROPOLIS) {
                         // bytes 0x3F where s_i s_j = +1, 0xBF where -1
