@@ -37,7 +37,7 @@ import workloads as W  # noqa: E402
 METRIC = "spin updates/ns and PTHR sweeps/s at L=16 (FP32 batched vs plain)"
 UNIT = "spin-updates/ns"
 WL = W.WORKLOADS["c4"]      # the headline workload; --workload selects another for reports
-# Algorithmic ALU work of one Metropolis spin update (see DESIGN.md): a
+# Algorithmic ALU work of one Metropolis spin update: a
 # quarter of a Philox4x32-10 call (10 rounds x (4 multiply halves + 2
 # three-input XORs) / 4 = 15), the 24-bit uniform (2), the local field
 # (6 FMA), -beta dE (2 FMUL), the exponential (1), the two comparisons (2)

@@ -31,8 +31,7 @@
  *   Sec. 5 (round trips) T_max -> T_min -> T_max excursions of a clone.
  *   App. A.1             Delta E = 2 s_i sum_j J_ij s_j, Metropolis
  *                        acceptance min{1, exp(-Delta E / T)}.
- * Readings where the paper is silent are listed in the design doc and repeated at
- * the point of use below.
+ * Readings where the paper is silent are stated at the point of use below.
  */
 #include <math.h>
 #include <stdint.h>
