@@ -381,13 +381,21 @@ sweep_kernel(SweepArgs a) {
 #pragma unroll
     for (int jj = 0; jj < KT; ++jj) nfl[jj] = 0u;
 
+    // one group per colour (G <= 512): its geometry in both colours, once
+    // (not where two blocks share an SM: there the registers are short)
+    constexpr bool ONE_G = G <= 512 && SweepBounds<L, RULE>::min_blocks == 1;
+    GroupGeo qc0{}, qc1{};
+    if (ONE_G) {
+        qc0 = group_geo<L>(g0, 0);
+        qc1 = group_geo<L>(g0, 1);
+    }
     for (int sw = 0; sw < nsw; ++sw) {
         const uint32_t c3base = TAG_SWEEP | ((uint32_t)(sweep_base + sw) << 9);
         for (int c = 0; c < 2; ++c) {
             const uint32_t c3 = c3base | ((uint32_t)c << 8);
             for (int gi = 0; gi < GP; ++gi) {
                 const int g = g0 + gi * Gt;
-                const GroupGeo q = group_geo<L>(g, c);
+                const GroupGeo q = ONE_G ? (c ? qc1 : qc0) : group_geo<L>(g, c);
                 uint32_t ahi, alo;
                 mul_wide(0xD2511F53u, (uint32_t)g, ahi, alo);
                 const SweepRng rng = sweep_rng(ahi, alo, rng_elo, c3, rk0, rk1);
