@@ -406,18 +406,44 @@ sweep_kernel(SweepArgs a) {
                 const int rym = ((y + L - 1) % L) + L * z, rzm = y + L * ((z + L - 1) % L);
                 // couplings of the group's 4 sites: +x,-x,+y,-y,+z,-z
                 float Jc[4][6];
+                if (Gm::FULL) {
+                    // no row padding: the four sites' couplings of every
+                    // direction but -x are one aligned 16-byte load
+                    const float4 px = *reinterpret_cast<const float4 *>(Js + 4 * q.own);
+                    const float4 py = *reinterpret_cast<const float4 *>(Js + LB + 4 * q.own);
+                    const float4 pz = *reinterpret_cast<const float4 *>(Js + 2 * LB + 4 * q.own);
+                    const float4 my = *reinterpret_cast<const float4 *>(
+                        Js + LB + 4 * ((cc * ROWS + rym) * W) + 4 * j);
+                    const float4 mz = *reinterpret_cast<const float4 *>(
+                        Js + 2 * LB + 4 * ((cc * ROWS + rzm) * W) + 4 * j);
+                    const float vpx[4] = {px.x, px.y, px.z, px.w}, vpy[4] = {py.x, py.y, py.z, py.w};
+                    const float vpz[4] = {pz.x, pz.y, pz.z, pz.w}, vmy[4] = {my.x, my.y, my.z, my.w};
+                    const float vmz[4] = {mz.x, mz.y, mz.z, mz.w};
 #pragma unroll
-                for (int kk = 0; kk < 4; ++kk) {
-                    int m = 4 * j + kk;
-                    if (m >= Lh) m = Lh - 1;
-                    const int so = 4 * q.own + kk;
-                    const int mxm = q.par ? m : (m + Lh - 1) % Lh;
-                    Jc[kk][0] = Js[so];
-                    Jc[kk][1] = Js[4 * ((cc * ROWS + r) * W) + mxm];
-                    Jc[kk][2] = Js[LB + so];
-                    Jc[kk][3] = Js[LB + 4 * ((cc * ROWS + rym) * W) + m];
-                    Jc[kk][4] = Js[2 * LB + so];
-                    Jc[kk][5] = Js[2 * LB + 4 * ((cc * ROWS + rzm) * W) + m];
+                    for (int kk = 0; kk < 4; ++kk) {
+                        const int m = 4 * j + kk;
+                        const int mxm = q.par ? m : (m + Lh - 1) % Lh;
+                        Jc[kk][0] = vpx[kk];
+                        Jc[kk][1] = Js[4 * ((cc * ROWS + r) * W) + mxm];
+                        Jc[kk][2] = vpy[kk];
+                        Jc[kk][3] = vmy[kk];
+                        Jc[kk][4] = vpz[kk];
+                        Jc[kk][5] = vmz[kk];
+                    }
+                } else {
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk) {
+                        int m = 4 * j + kk;
+                        if (m >= Lh) m = Lh - 1;
+                        const int so = 4 * q.own + kk;
+                        const int mxm = q.par ? m : (m + Lh - 1) % Lh;
+                        Jc[kk][0] = Js[so];
+                        Jc[kk][1] = Js[4 * ((cc * ROWS + r) * W) + mxm];
+                        Jc[kk][2] = Js[LB + so];
+                        Jc[kk][3] = Js[LB + 4 * ((cc * ROWS + rym) * W) + m];
+                        Jc[kk][4] = Js[2 * LB + so];
+                        Jc[kk][5] = Js[2 * LB + 4 * ((cc * ROWS + rzm) * W) + m];
+                    }
                 }
                 // the same couplings as packed pairs (sites 0,1 and 2,3); the x
                 // pair is ordered as (aligned word xa, shifted word xs), so the
