@@ -107,45 +107,46 @@ __device__ __forceinline__ void overlap_counts(const uint32_t *A, const uint32_t
     }
 }
 
-constexpr int MEASURE_MAX_WARPS = 8;   // threads per measurement block <= 256
+constexpr int MEASURE_WARPS = 8;   // (sample, temperature) items per measurement block
 
-// One block per (sample, temperature index k).  Accumulator layout per
-// (s, k): [0] measurements, [1] sum e, [2] sum e^2 (over groups), [3] sum q,
-// [4] sum q^2, [5] sum q_l, [6] sum S, [7] sum q^4 (over pairs).
+// One warp per (sample, temperature index k), eight per block.  Accumulator
+// layout per (s, k): [0] measurements, [1] sum e, [2] sum e^2 (over groups),
+// [3] sum q, [4] sum q^2, [5] sum q_l, [6] sum S, [7] sum q^4 (over pairs).
 //
-// Phase 1: every thread counts overlaps of every replica pair (and the chaos
-// pair); phase 2: warp 0 evaluates the FP64 quantities of the groups and
-// pairs on separate lanes, and lane 0 adds them to the accumulators in the
-// fixed order (groups, then pairs) with one IEEE rounding per operation.
+// The warp counts the overlaps of every replica pair (and the chaos pair);
+// lane P keeps pair P's counts.  Then the FP64 quantities of the groups and
+// pairs are evaluated on separate lanes, and lane 0 adds them to the
+// accumulators in the fixed order (groups, then pairs) with one IEEE
+// rounding per operation.  No shared memory and no block barrier.
 template <int L>
-__global__ void measure_kernel(Batch b, int first, int chaos) {
+__global__ void __launch_bounds__(32 * MEASURE_WARPS) measure_kernel(Batch b, int first, int count,
+                                                                     int chaos) {
     using Gm = Geom<L>;
     constexpr int V = Gm::V, LW = Gm::LAT_WORDS;
-    const int s = first + blockIdx.x;
-    const int k = blockIdx.y;
+    const int lane = threadIdx.x & 31;
+    const int item = blockIdx.x * MEASURE_WARPS + (threadIdx.x >> 5);
+    if (item >= count * b.NT) return;                 // warp-uniform
+    const int s = first + item / b.NT, k = item % b.NT;
     if (!b.active[s]) return;
-    __shared__ int s_cnt[3][16][MEASURE_MAX_WARPS];   // [nneg, ndiff, chaos nneg][pair][warp]
-    const int tid = threadIdx.x, T = blockDim.x, lane = tid & 31, wid = tid >> 5;
     const int32_t *perm = b.perm + (size_t)s * b.NR * b.NSLOT;
     const uint32_t *spins = b.spins + (size_t)s * b.NLAT * LW;
+    int tn = 0, td = 0, tc = 0;                       // pair `lane`'s counts
     for (int P = 0; P < b.NPAIR; ++P) {
         const int la = 2 * P * b.NSLOT + perm[2 * P * b.NSLOT + k];
         const int lb = (2 * P + 1) * b.NSLOT + perm[(2 * P + 1) * b.NSLOT + k];
         int nneg, ndiff, cneg = 0;
-        overlap_counts<L>(spins + (size_t)la * LW, spins + (size_t)lb * LW, tid, T, nneg, ndiff);
+        overlap_counts<L>(spins + (size_t)la * LW, spins + (size_t)lb * LW, lane, 32, nneg, ndiff);
         if (chaos) {
             // temperature chaos: clone of group 2P at T_0 against group 2P+1 at T_k
             const int l0 = 2 * P * b.NSLOT + perm[2 * P * b.NSLOT];
             int cdiff;
-            overlap_counts<L>(spins + (size_t)l0 * LW, spins + (size_t)lb * LW, tid, T, cneg, cdiff);
+            overlap_counts<L>(spins + (size_t)l0 * LW, spins + (size_t)lb * LW, lane, 32, cneg, cdiff);
         }
         nneg = __reduce_add_sync(0xffffffffu, nneg);
         ndiff = __reduce_add_sync(0xffffffffu, ndiff);
         cneg = __reduce_add_sync(0xffffffffu, cneg);
-        if (lane == 0) { s_cnt[0][P][wid] = nneg; s_cnt[1][P][wid] = ndiff; s_cnt[2][P][wid] = cneg; }
+        if (lane == P) { tn = nneg; td = ndiff; tc = cneg; }
     }
-    __syncthreads();
-    if (wid != 0) return;
     // per-group energy density on lane g, per-pair overlaps on lane P
     double e = 0.0, q = 0.0, ql = 0.0, S = 0.0, qc = 0.0;
     // e = H / V (exact scaling when V is a power of two); q, q_l and T_k
@@ -156,8 +157,6 @@ __global__ void measure_kernel(Batch b, int first, int chaos) {
         e = ((V & (V - 1)) == 0) ? __dmul_rn(H, 1.0 / (double)V) : __ddiv_rn(H, (double)V);
     }
     if (lane < b.NPAIR) {
-        int tn = 0, td = 0, tc = 0;
-        for (int w = 0; w < T / 32; ++w) { tn += s_cnt[0][lane][w]; td += s_cnt[1][lane][w]; tc += s_cnt[2][lane][w]; }
         const double Tk = b.tabT[k];
         const int la = 2 * lane * b.NSLOT + perm[2 * lane * b.NSLOT + k];
         q = b.tabQ[tn];
@@ -217,11 +216,12 @@ cudaError_t launch_swap(const Batch &b, int flags, int first, int count, cudaStr
 
 cudaError_t launch_measure(const Batch &b, int first, int count, int chaos, cudaStream_t st) {
     if (b.NR > 32) return cudaErrorInvalidValue;
-    dim3 grid(count, b.NT);
-    // about two packed words per thread, 64..256 threads
-    int threads = ((lattice_words(b.L) / 2 + 31) / 32) * 32;
-    threads = threads < 64 ? 64 : (threads > 32 * MEASURE_MAX_WARPS ? 32 * MEASURE_MAX_WARPS : threads);
-#define X(LL) if (b.L == LL) { measure_kernel<LL><<<grid, threads, 0, st>>>(b, first, chaos); return cudaGetLastError(); }
+    const long items = (long)count * b.NT;
+    if (items <= 0) return cudaSuccess;
+    const int blocks = (int)((items + MEASURE_WARPS - 1) / MEASURE_WARPS);
+#define X(LL) if (b.L == LL) { \
+        measure_kernel<LL><<<blocks, 32 * MEASURE_WARPS, 0, st>>>(b, first, count, chaos); \
+        return cudaGetLastError(); }
     PTHR_FOR_EACH_L(X)
 #undef X
     return cudaErrorInvalidValue;
