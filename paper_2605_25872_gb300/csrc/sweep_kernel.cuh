@@ -316,30 +316,69 @@ sweep_kernel(SweepArgs a) {
         for (int i = tid; i < 3 * LB; i += T) Js[i] = 0.f;
     __syncthreads();     // lattice ids and zeroed row padding visible
     bool on_grid = true;
-    constexpr int JU = 4;
-    for (int i0 = tid; i0 < Gm::V; i0 += JU * T) {
-        float jv[JU][3];
+    if (L % 4 == 0) {
+        // four consecutive sites x0..x0+3 (x0 a multiple of 4) of one x row
+        // per 16-byte load: they alternate colours, and sites x0, x0+2 (and
+        // x0+1, x0+3) are adjacent bytes m0, m0+1 of one packed word
+        constexpr int JQ = 2;
+        for (int t0 = tid; t0 < Gm::V / 4; t0 += JQ * T) {
+            float4 jv[JQ][3];
 #pragma unroll
-        for (int u = 0; u < JU; ++u) {
-            const int i = i0 + u * T;
-            if (i < Gm::V) {
-                jv[u][0] = __ldg(Jg + i);
-                jv[u][1] = __ldg(Jg + Gm::V + i);
-                jv[u][2] = __ldg(Jg + 2 * Gm::V + i);
+            for (int u = 0; u < JQ; ++u) {
+                const int t = t0 + u * T;
+                if (t < Gm::V / 4) {
+#pragma unroll
+                    for (int d = 0; d < 3; ++d)
+                        jv[u][d] = __ldg(reinterpret_cast<const float4 *>(Jg + d * Gm::V) + t);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < JQ; ++u) {
+                const int t = t0 + u * T;
+                if (t < Gm::V / 4) {
+                    const int i = 4 * t;
+                    const int x0 = i % L, r = i / L;
+                    const int c0 = (x0 + r % L + r / L) & 1;
+                    const int m0 = x0 >> 1;
+                    const int s0 = 4 * ((c0 * ROWS + r) * W + (m0 >> 2)) + (m0 & 3);
+                    const int s1 = 4 * (((c0 ^ 1) * ROWS + r) * W + (m0 >> 2)) + (m0 & 3);
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) {
+                        const float4 v = jv[u][d];
+                        *reinterpret_cast<float2 *>(Js + d * LB + s0) = make_float2(v.x, v.z);
+                        *reinterpret_cast<float2 *>(Js + d * LB + s1) = make_float2(v.y, v.w);
+                        on_grid = on_grid && on_coupling_grid(v.x) && on_coupling_grid(v.y) &&
+                                  on_coupling_grid(v.z) && on_coupling_grid(v.w);
+                    }
+                }
             }
         }
+    } else {
+        constexpr int JU = 4;
+        for (int i0 = tid; i0 < Gm::V; i0 += JU * T) {
+            float jv[JU][3];
 #pragma unroll
-        for (int u = 0; u < JU; ++u) {
-            const int i = i0 + u * T;
-            if (i < Gm::V) {
-                int w, by;
-                site_slot<L>(i, w, by);
-                const int slot = 4 * w + by;
-                Js[slot] = jv[u][0];
-                Js[LB + slot] = jv[u][1];
-                Js[2 * LB + slot] = jv[u][2];
-                on_grid = on_grid && on_coupling_grid(jv[u][0]) && on_coupling_grid(jv[u][1]) &&
-                          on_coupling_grid(jv[u][2]);
+            for (int u = 0; u < JU; ++u) {
+                const int i = i0 + u * T;
+                if (i < Gm::V) {
+                    jv[u][0] = __ldg(Jg + i);
+                    jv[u][1] = __ldg(Jg + Gm::V + i);
+                    jv[u][2] = __ldg(Jg + 2 * Gm::V + i);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < JU; ++u) {
+                const int i = i0 + u * T;
+                if (i < Gm::V) {
+                    int w, by;
+                    site_slot<L>(i, w, by);
+                    const int slot = 4 * w + by;
+                    Js[slot] = jv[u][0];
+                    Js[LB + slot] = jv[u][1];
+                    Js[2 * LB + slot] = jv[u][2];
+                    on_grid = on_grid && on_coupling_grid(jv[u][0]) && on_coupling_grid(jv[u][1]) &&
+                              on_coupling_grid(jv[u][2]);
+                }
             }
         }
     }
