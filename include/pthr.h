@@ -63,7 +63,9 @@ typedef enum {
     PTHR_E_CUDA = 3,         /* a CUDA runtime call or launch failed               */
     PTHR_E_NOCONVERGE = 4,   /* a bounded device loop hit its iteration cap        */
     PTHR_E_TIMEOUT = 5,      /* pthr_poll() timed out before the stream drained    */
-    PTHR_E_STATE = 6         /* call not valid now (e.g. during stream capture)    */
+    PTHR_E_STATE = 6,        /* call not valid now (e.g. during stream capture)    */
+    PTHR_E_BOUNDS = 7        /* a device-side range check failed (the work it
+                                guarded was skipped, nothing was written)          */
 } pthr_status;
 
 enum { PTHR_METROPOLIS = 0, PTHR_HEATBATH = 1 };
@@ -93,6 +95,9 @@ enum { PTHR_OBS_MEASURE = 1, PTHR_OBS_READ_HOST = 2, PTHR_OBS_READ_DEVICE = 4, P
  *  CSTAT  int64    [S][n_pairs][n_temps][4] cluster statistics of the last
  *                                   cluster move: clusters, largest, second
  *                                   largest, sites flipped
+ *  PRETH  uint32   [S]              reservoir pre-thermalisation sweeps done since
+ *                                   the sample was created or reset (the sweep
+ *                                   index of the next pre-thermalisation sweep)
  *  CHAOS  double   [S][n_temps][2]  temperature-chaos accumulators: count and
  *                                   sum over pairs of q^2 between the clone of
  *                                   group 2p at T_0 and the clone of group 2p+1
@@ -107,7 +112,7 @@ enum {
     PTHR_BUF_J = 0, PTHR_BUF_SPINS, PTHR_BUF_ENERGY, PTHR_BUF_PERM, PTHR_BUF_AGE,
     PTHR_BUF_RT, PTHR_BUF_TRIPS, PTHR_BUF_PTACC, PTHR_BUF_FLIPS, PTHR_BUF_OBS,
     PTHR_BUF_EMCS, PTHR_BUF_SEEDS, PTHR_BUF_ACTIVE, PTHR_BUF_STATUS, PTHR_BUF_CSTAT,
-    PTHR_BUF_CHAOS, PTHR_BUF_TABLES, PTHR_NBUF
+    PTHR_BUF_CHAOS, PTHR_BUF_PRETH, PTHR_BUF_TABLES, PTHR_NBUF
 };
 
 typedef struct {
@@ -227,13 +232,19 @@ PTHR_API pthr_status pthr_emcs(pthr_batch *b, int n, int use_graph);
 
 /* n_sweeps sweeps at T_max of every reservoir clone before EMCS 0 (Sec. 3:
  * the reservoir refreshes clones for 960 sweeps); uses EMCS counter word
- * 0xFFFFFFFF.  Only the samples in [first, first+count). */
+ * 0xFFFFFFFF.  Only the samples in [first, first+count).  The sweep index
+ * continues from the sample's PRETH counter, so two calls of n sweeps equal
+ * one call of 2n (fresh random numbers, never a replay); the counter restarts
+ * at creation and at pthr_reset_samples.  A sample whose counter would pass
+ * 2^23 is skipped and pthr_poll() then returns PTHR_E_BOUNDS. */
 PTHR_API pthr_status pthr_prethermalize_reservoir(pthr_batch *b, int first, int count,
                                                   int n_sweeps);
 
 /* Wait up to timeout_ms (< 0: forever) for the stream to drain, then return
- * the latched device status (PTHR_E_NOCONVERGE if a device loop hit its cap),
- * or PTHR_E_TIMEOUT.  Clears the status word after reading it. */
+ * the latched device status (PTHR_E_NOCONVERGE if a device loop hit its cap,
+ * PTHR_E_BOUNDS if a device range check failed), or PTHR_E_TIMEOUT if the
+ * stream is still busy (the status word is then left for a later poll).
+ * Clears the status word after reading it. */
 PTHR_API pthr_status pthr_poll(pthr_batch *b, int timeout_ms);
 
 /* Spins of every clone in natural order, int8 +1/-1, [S][n_lat][V], device

@@ -235,6 +235,7 @@ class OracleSample:
         self.n_ties = np.zeros(2, dtype=np.int64)
         self.obs = np.zeros((n_temps, len(OBS_FIELDS)))
         self.emcs_done = 0
+        self.pretherm_done = 0    # reservoir pre-thermalisation sweeps so far
 
     def _state(self):
         return _State(*(a.ctypes.data for a in (self.spins, self.perm, self.E_lat, self.age,
@@ -242,14 +243,16 @@ class OracleSample:
                                                 self.flips, self.n_ties, self.obs)))
 
     def prethermalize_reservoir(self, n_sweeps):
-        """n_sweeps at T_max of every reservoir clone, EMCS counter word 2^32-1."""
+        """n_sweeps at T_max of every reservoir clone, EMCS counter word 2^32-1;
+        the sweep index continues over successive calls."""
         for g in range(self.n_groups):
             for r in range(self.n_res):
                 lat = g * self.nslot + int(self.perm[g * self.nslot + self.n_temps + r])
                 for sw in range(n_sweeps):
                     sweep(self.L, self.J, self.spins[lat], self.beta[-1], self.seed, lat,
-                          PRETHERM_EMCS, sw, self.cfg.order, self.cfg.rule)
+                          PRETHERM_EMCS, self.pretherm_done + sw, self.cfg.order, self.cfg.rule)
                 self.E_lat[lat] = energy(self.L, self.J, self.spins[lat])
+        self.pretherm_done += n_sweeps
 
     def emcs(self, n=1):
         st = self._state()

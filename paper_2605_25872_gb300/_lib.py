@@ -12,9 +12,10 @@ import os
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libpthr.so")
 
-PTHR_OK, PTHR_E_INVAL, PTHR_E_NOMEM, PTHR_E_CUDA, PTHR_E_NOCONVERGE, PTHR_E_TIMEOUT, PTHR_E_STATE = range(7)
+(PTHR_OK, PTHR_E_INVAL, PTHR_E_NOMEM, PTHR_E_CUDA, PTHR_E_NOCONVERGE, PTHR_E_TIMEOUT, PTHR_E_STATE,
+ PTHR_E_BOUNDS) = range(8)
 STATUS_NAMES = {0: "PTHR_OK", 1: "PTHR_E_INVAL", 2: "PTHR_E_NOMEM", 3: "PTHR_E_CUDA",
-                4: "PTHR_E_NOCONVERGE", 5: "PTHR_E_TIMEOUT", 6: "PTHR_E_STATE"}
+                4: "PTHR_E_NOCONVERGE", 5: "PTHR_E_TIMEOUT", 6: "PTHR_E_STATE", 7: "PTHR_E_BOUNDS"}
 METROPOLIS, HEATBATH = 0, 1
 CLUSTER_OFF, CLUSTER_ACU, CLUSTER_SINGLE = 0, 1, 2
 SWAP_PT, SWAP_ER = 1, 2
@@ -22,7 +23,8 @@ OBS_MEASURE, OBS_READ_HOST, OBS_READ_DEVICE, OBS_RESET, OBS_CHAOS = 1, 2, 4, 8, 
 NOBS = 8
 MAX_L = 24
 (BUF_J, BUF_SPINS, BUF_ENERGY, BUF_PERM, BUF_AGE, BUF_RT, BUF_TRIPS, BUF_PTACC, BUF_FLIPS,
- BUF_OBS, BUF_EMCS, BUF_SEEDS, BUF_ACTIVE, BUF_STATUS, BUF_CSTAT, BUF_CHAOS, BUF_TABLES, NBUF) = range(18)
+ BUF_OBS, BUF_EMCS, BUF_SEEDS, BUF_ACTIVE, BUF_STATUS, BUF_CSTAT, BUF_CHAOS, BUF_PRETH, BUF_TABLES,
+ NBUF) = range(19)
 
 # every exported entry point of include/pthr.h
 EXPORTS = ("pthr_required_bytes", "pthr_buffer_info", "pthr_lattice_bytes", "pthr_create_batch",

@@ -124,6 +124,7 @@ Layout make_layout(const pthr_config *c) {
     l.len[PTHR_BUF_STATUS] = 4 * sizeof(uint32_t);
     l.len[PTHR_BUF_CSTAT] = S * NP * NT * 4 * sizeof(long long);
     l.len[PTHR_BUF_CHAOS] = S * NT * 2 * sizeof(double);
+    l.len[PTHR_BUF_PRETH] = S * sizeof(uint32_t);
     l.len[PTHR_BUF_TABLES] = (2 * NT + 4 * V + 2) * sizeof(double) + NT * sizeof(float);
     size_t o = 0;
     for (int i = 0; i < PTHR_NBUF; ++i) {
@@ -215,6 +216,8 @@ pthr_status do_sweep(pthr_batch *b, int n_pt, int n_res, int first, int count, i
     if (smem > 220 * 1024)
         return fail(b, PTHR_E_INVAL, "sweep block needs %zu bytes of shared memory; lower the lattices per block", smem);
     CUDA_TRY(b, launch_sweep(a, blocks, sh.threads, sh.KT, b->stream), "sweep launch");
+    if (pretherm)   // the next pre-thermalisation sweeps continue the index
+        CUDA_TRY(b, launch_advance_pretherm(b->dev, first, count, n_res, b->stream), "pretherm counter");
     return PTHR_OK;
 }
 
@@ -337,6 +340,7 @@ PTHR_API pthr_status pthr_create_batch(const pthr_config *cfg, void *device_work
     d.status = (uint32_t *)(base + l.off[PTHR_BUF_STATUS]);
     d.cstat = (long long *)(base + l.off[PTHR_BUF_CSTAT]);
     d.chaos = (double *)(base + l.off[PTHR_BUF_CHAOS]);
+    d.preth = (uint32_t *)(base + l.off[PTHR_BUF_PRETH]);
     double *tab = (double *)(base + l.off[PTHR_BUF_TABLES]);
     const int NTt = cfg->n_temps, Vt = cfg->L * cfg->L * cfg->L;
     d.tabT = tab;
@@ -566,7 +570,7 @@ PTHR_API pthr_status pthr_poll(pthr_batch *b, int timeout_ms) {
     CUDA_TRY(b, cudaMemcpy(st, b->dev.status, sizeof(st), cudaMemcpyDeviceToHost), "status read");
     CUDA_TRY(b, cudaMemset(b->dev.status, 0, sizeof(st)), "status clear");
     if (st[0] & STATUS_NOCONVERGE) return fail(b, PTHR_E_NOCONVERGE, "a cluster labelling loop hit its iteration cap");
-    if (st[0] & STATUS_BOUNDS) return fail(b, PTHR_E_NOCONVERGE, "a device bounds check failed");
+    if (st[0] & STATUS_BOUNDS) return fail(b, PTHR_E_BOUNDS, "a device range check failed (the guarded work was skipped)");
     return PTHR_OK;
 }
 
@@ -688,6 +692,7 @@ PTHR_API pthr_status pthr_group_create(pthr_batch *const *batches, int n, void *
     cudaError_t e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
     for (int i = 0; i < n && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&join[i], cudaEventDisableTiming);
     pthr_status st = PTHR_OK;
+    int failed = -1;   // batch whose EMCS could not be captured
     cudaGraph_t g = nullptr;
     if (e == cudaSuccess) e = cudaStreamBeginCapture(master, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
@@ -695,6 +700,7 @@ PTHR_API pthr_status pthr_group_create(pthr_batch *const *batches, int n, void *
         for (int i = 0; i < n && e == cudaSuccess && st == PTHR_OK; ++i) {
             e = cudaStreamWaitEvent(batches[i]->stream, fork, 0);
             if (e == cudaSuccess) st = one_emcs(batches[i]);
+            if (st != PTHR_OK) failed = i;
             if (e == cudaSuccess && st == PTHR_OK) e = cudaEventRecord(join[i], batches[i]->stream);
             if (e == cudaSuccess && st == PTHR_OK) e = cudaStreamWaitEvent(master, join[i], 0);
         }
@@ -708,7 +714,7 @@ PTHR_API pthr_status pthr_group_create(pthr_batch *const *batches, int n, void *
     delete[] join;
     if (st != PTHR_OK || e != cudaSuccess) {
         if (g) cudaGraphDestroy(g);
-        if (st != PTHR_OK) return fail(nullptr, st, "%s", batches[0]->err);
+        if (st != PTHR_OK) return fail(nullptr, st, "batch %d: %s", failed, batches[failed]->err);
         return cuda_fail(nullptr, e, "group capture");
     }
     pthr_group *grp = new pthr_group();

@@ -91,8 +91,18 @@ __global__ void init_meta_kernel(Batch b, int first, int count) {
     for (int i = threadIdx.x; i < ncs; i += blockDim.x) b.cstat[(size_t)s * ncs + i] = 0;
     if (threadIdx.x == 0) {
         b.emcs[s] = 0u;
+        b.preth[s] = 0u;
         b.active[s] = 1;
     }
+}
+
+// After a pre-thermalisation launch of n sweeps: the next one continues the
+// sweep index (the launch itself skipped a sample whose index would pass 2^23).
+__global__ void advance_pretherm_kernel(Batch b, int first, int count, int n) {
+    const int s = first + blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= first + count || !b.active[s]) return;
+    const uint32_t p = b.preth[s];
+    if ((unsigned long long)p + (unsigned long long)n < (1ull << 23)) b.preth[s] = p + (uint32_t)n;
 }
 
 __global__ void export_kernel(Batch b, int8_t *out) {
@@ -148,6 +158,12 @@ cudaError_t launch_init_state(const Batch &b, int first, int count, cudaStream_t
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     init_meta_kernel<<<count, 256, 0, st>>>(b, first, count);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_advance_pretherm(const Batch &b, int first, int count, int n_sweeps, cudaStream_t st) {
+    if (count <= 0) return cudaSuccess;
+    advance_pretherm_kernel<<<(count + 255) / 256, 256, 0, st>>>(b, first, count, n_sweeps);
     return cudaGetLastError();
 }
 

@@ -13,7 +13,8 @@ struct SweepArgs {
     int pt_tasks, res_tasks;             // blocks per sample per kind
     int do_pt, do_res;                   // launch PT / reservoir blocks (0/1)
     int sample_first, sample_count;
-    int emcs_override;                   // 1: counter word PRETHERM_EMCS
+    int emcs_override;                   // 1: counter word PRETHERM_EMCS, sweep index
+                                         //    from the sample's PRETH counter
     int Gt;                              // groups per lattice lane (divides G and threads)
 };
 
@@ -41,6 +42,7 @@ cudaError_t launch_measure(const Batch &b, int first, int count, int chaos, cuda
 // init.cu
 cudaError_t launch_couplings_from_seed(const Batch &b, int first, int count, cudaStream_t st);
 cudaError_t launch_init_state(const Batch &b, int first, int count, cudaStream_t st);
+cudaError_t launch_advance_pretherm(const Batch &b, int first, int count, int n_sweeps, cudaStream_t st);
 cudaError_t launch_export_spins(const Batch &b, int8_t *out, cudaStream_t st);
 cudaError_t launch_import_spins(const Batch &b, const int8_t *in, cudaStream_t st);
 

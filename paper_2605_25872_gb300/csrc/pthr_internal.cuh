@@ -69,6 +69,7 @@ struct Batch {
     uint32_t *status;         // [4]
     long long *cstat;         // [S][NPAIR][NT][4]
     double *chaos;            // [S][NT][2]
+    uint32_t *preth;          // [S]     reservoir pre-thermalisation sweeps done
     const double *tabT;       // [NT]    T_k
     const double *tabBeta;    // [NT]    1 / T_k
     const double *tabQ;       // [V+1]   (V - 2n) / V

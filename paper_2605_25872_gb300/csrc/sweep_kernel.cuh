@@ -275,7 +275,17 @@ sweep_kernel(SweepArgs a) {
     const int K = min(Kmax, total - e0);
     if (K <= 0) return;
     const int nsw = kind ? a.n_res_sweeps : a.n_pt_sweeps;
-    const int sweep_base = kind ? a.res_sweep_base : a.pt_sweep_base;
+    int sweep_base = kind ? a.res_sweep_base : a.pt_sweep_base;
+    if (a.emcs_override) {
+        // pre-thermalisation continues the sample's own sweep index; an index
+        // past the counter's 23 bits would repeat random numbers: skip
+        const uint32_t p = b.preth[s];
+        if ((unsigned long long)p + (unsigned long long)nsw >= (1ull << 23)) {
+            if (threadIdx.x == 0) set_status(b.status, STATUS_BOUNDS);
+            return;
+        }
+        sweep_base = (int)p;
+    }
     const uint32_t emcs = a.emcs_override ? PRETHERM_EMCS : b.emcs[s];
     const unsigned long long seed = b.seeds[s];
     const int tid = threadIdx.x, T = blockDim.x;

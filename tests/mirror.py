@@ -46,12 +46,13 @@ class Mirror:
                     self.n_acu = k + 1
         self.pt_off = 0
         self.res_off = 0
-        self.decisions = 0
-        self.ties = []        # (sample, lattice, sweep_global, site) for this call
+        self.decisions = 0    # local accept decisions taken so far
+        self.n_ties = 0       # near-tie local decisions among them
 
     # ---------------------------------------------------------------- sweeps
     def sweep(self, n_pt, n_res, emcs_override=None, samples=None, pretherm=False):
-        """Returns {(s, lat): set(tie sites)} for this call."""
+        """Returns {(s, lat): set(tie sites)} for this call.  Pre-thermalisation
+        sweeps continue each sample's own pre-thermalisation sweep index."""
         c = self.cfg
         ties = {}
         for s in (range(c.n_samples) if samples is None else samples):
@@ -65,7 +66,7 @@ class Mirror:
                         continue
                     lat = smp.lattice_at(g, pos)
                     b = self.beta[-1] if in_res else self.beta[pos]
-                    base = 0 if pretherm else (self.res_off if in_res else self.pt_off)
+                    base = smp.pretherm_done if pretherm else (self.res_off if in_res else self.pt_off)
                     for sw in range(nsw):
                         acc, tl, dE = O.sweep(self.L, smp.J, smp.spins[lat], b, smp.seed, lat,
                                               emcs & 0xFFFFFFFF, base + sw, rule=self.rule,
@@ -73,9 +74,12 @@ class Mirror:
                                               field_err_bound=self.field_err_bound)
                         smp.flips[lat] += acc
                         self.decisions += self.V
+                        self.n_ties += len(tl)
                         if len(tl):
                             ties.setdefault((s, lat), set()).update(int(t) for t in tl)
                     smp.E_lat[lat] = O.energy(self.L, smp.J, smp.spins[lat])
+            if pretherm:
+                smp.pretherm_done += n_res
         if not pretherm:
             self.pt_off += n_pt
             self.res_off += n_res
@@ -106,17 +110,19 @@ class Mirror:
 
     # ---------------------------------------------------------------- PT / ER
     def swap(self, pt=True, er=None):
+        """Returns {sample: near-tie PT decisions} for this call."""
         c = self.cfg
         er = c.er_on if er is None else er
-        pt_ties = 0
-        for smp in self.samples:
+        pt_ties = {}
+        for s, smp in enumerate(self.samples):
             for g in range(c.n_replicas):
                 perm = smp.perm[g * smp.nslot:(g + 1) * smp.nslot]
                 if pt:
                     Ep = np.array([smp.E_lat[g * smp.nslot + perm[q]] for q in range(smp.nslot)])
                     acc, nt = O.pt_round(self.beta, perm, Ep, smp.seed, g,
                                          smp.emcs_done & 0xFFFFFFFF, self.tie_eps)
-                    pt_ties += nt
+                    if nt:
+                        pt_ties[s] = pt_ties.get(s, 0) + nt
                     smp.pt_accepted[g * c.n_temps:(g + 1) * c.n_temps] += acc
                     rs = smp.rt_state[g * smp.nslot:(g + 1) * smp.nslot]
                     if rs[perm[0]] & 1:

@@ -11,9 +11,11 @@ import test_oracle_pins as T  # noqa: E402
 
 PINS = [
     T.test_philox_known_answers,
+    lambda: T.test_temperature_grid_is_uniform_with_both_ends(12, 0.2, 1.6),
     T.test_energy_closed_forms_and_symmetries,
     T.test_enumeration_closed_forms,
     T.test_pair_observables_closed_forms,
+    T.test_pair_moments_enumeration_agrees_with_the_enumerator,
     T.test_sweep_incremental_energy_equals_recomputed,
     T.test_sweep_is_gauge_covariant,
     lambda: T.test_cc_labels_match_scipy(4),

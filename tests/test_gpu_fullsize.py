@@ -44,9 +44,7 @@ def run_sampled(wl, n_emcs, picks):
     for _ in range(n_emcs):
         gpu.emcs(1)
         ties, pt_ties = mir.emcs()
-        ties_seen |= {s for s, _ in ties}
-        if pt_ties:
-            ties_seen |= set(range(len(picks)))
+        ties_seen |= {s for s, _ in ties} | set(pt_ties)
     g = gpu.export_spins().cpu().numpy()[picks]
     o = mir.spins()
     gp = gpu.perm.cpu().numpy()[picks]

@@ -21,6 +21,27 @@ from paper_2605_25872_gb300 import Batch, BatchConfig  # noqa: E402
 from paper_2605_25872_gb300.build import build  # noqa: E402
 
 TIE_RATE_MAX = 1e-5
+# near ties and decisions of every sweep-parity run in this module, pooled:
+# the 1e-5 rate bound is checked on each run large enough to resolve it
+# (>= 1e6 decisions) and on the pool (test_pooled_near_tie_rate)
+TIE_LEDGER = {"ties": 0, "decisions": 0}
+
+
+def record_ties(mir):
+    TIE_LEDGER["ties"] += mir.n_ties
+    TIE_LEDGER["decisions"] += mir.decisions
+    if mir.decisions >= 1_000_000:
+        assert mir.n_ties < TIE_RATE_MAX * mir.decisions, (mir.n_ties, mir.decisions)
+
+
+def assert_explained(L, g, o, ties, it):
+    """Every (sample, lattice) whose spins differ had near ties in this call,
+    and every differing site is a tie site or (first colour) its neighbour."""
+    bad = np.argwhere(g != o)
+    for s, lat in {(int(a), int(b)) for a, b, _ in bad}:
+        sites = bad[(bad[:, 0] == s) & (bad[:, 1] == lat)][:, 2]
+        assert (s, lat) in ties and explained_by_ties(L, sites, ties[(s, lat)]), \
+            f"call {it}: sample {s} lattice {lat} differs at {sites[:10]} without a near tie"
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -61,25 +82,22 @@ def resync(gpu, mir):
 
 def check_sweep_parity(gpu, mir, n_calls, n_pt=1, n_res=1):
     """Sweep both sides call by call; returns (near ties that changed the
-    trajectory, oracle decisions)."""
-    L = mir.L
+    trajectory, oracle decisions).  The near-tie count itself must stay below
+    1e-5 of the decisions (record_ties)."""
+    assert n_pt <= 1 and n_res <= 1   # one sweep per call: tie explanations are local
     diverged = 0
     for it in range(n_calls):
         gpu.sweep(n_pt, n_res)
         ties = mir.sweep(n_pt, n_res)
         g = gpu_spins(gpu)
         o = mir.spins()
-        bad = np.argwhere(g != o)
-        if len(bad):
-            for s, lat in {(int(a), int(b)) for a, b, _ in bad}:
-                sites = bad[(bad[:, 0] == s) & (bad[:, 1] == lat)][:, 2]
-                assert (s, lat) in ties and (n_pt + n_res) <= 2 and \
-                    explained_by_ties(L, sites, ties[(s, lat)]), \
-                    f"call {it}: sample {s} lattice {lat} differs at {sites[:10]} without a near tie"
+        if not np.array_equal(g, o):
+            assert_explained(mir.L, g, o, ties, it)
             diverged += 1
             resync(gpu, mir)
         else:
             np.testing.assert_array_equal(gpu.energies.cpu().numpy(), mir.energies())
+    record_ties(mir)
     return diverged, mir.decisions
 
 
@@ -281,6 +299,13 @@ def test_cluster_move_energies_outside_the_exact_grid(kind):
 
 # ----------------------------------------------------------------------------- a7/a8/a9 and full EMCS
 
+def diverged_samples(gpu, mir):
+    g = gpu_spins(gpu)
+    bad = {int(a) for a, _, _ in np.argwhere(g != mir.spins())}
+    bad |= {int(a) for a in np.argwhere((gpu.perm.cpu().numpy() != mir.perms()).any(axis=(1, 2))).ravel()}
+    return bad
+
+
 def run_emcs_parity(cfg, n_emcs, seed):
     gpu, mir = make(cfg, seed=seed)
     resyncs = 0
@@ -291,14 +316,12 @@ def run_emcs_parity(cfg, n_emcs, seed):
         gpu.swap(True, cfg.er_on)
         gpu.measure()
         ties, pt_ties = mir.emcs()
-        g = gpu_spins(gpu)
-        same = (np.array_equal(g, mir.spins()) and np.array_equal(gpu.perm.cpu().numpy(), mir.perms()))
-        if not same:
-            bad_samples = {int(a) for a, _, _ in np.argwhere(g != mir.spins())}
-            bad_samples |= {int(a) for a in np.argwhere((gpu.perm.cpu().numpy() != mir.perms()).any(axis=(1, 2))).ravel()}
-            tie_samples = {s for s, _ in ties}
-            assert bad_samples <= tie_samples or pt_ties > 0, \
-                f"EMCS {e}: samples {bad_samples} diverged without a near tie"
+        bad_samples = diverged_samples(gpu, mir)
+        if bad_samples:
+            # a near tie of a sample (local or PT) may change that sample only
+            tie_samples = {s for s, _ in ties} | set(pt_ties)
+            assert bad_samples <= tie_samples, \
+                f"EMCS {e}: samples {bad_samples - tie_samples} diverged without a near tie of their own"
             resyncs += 1
             resync(gpu, mir)
             gpu.obs.copy_(torch.from_numpy(np.stack([s.obs for s in mir.samples])))
@@ -312,6 +335,7 @@ def run_emcs_parity(cfg, n_emcs, seed):
                                       np.stack([s.pt_accepted for s in mir.samples]))
         np.testing.assert_array_equal(gpu.obs.cpu().numpy(), np.stack([s.obs for s in mir.samples]))
         assert np.all(gpu.emcs_counter.cpu().numpy() == e + 1)
+    record_ties(mir)
     return gpu, mir, resyncs
 
 
@@ -431,14 +455,44 @@ def test_idle_slots_are_untouched():
 
 
 def test_prethermalisation_matches_oracle():
+    """Reservoir pre-thermalisation one sweep per call: the sweep index
+    continues from call to call, so 30 calls of one sweep are the oracle's 30
+    sweeps.  A divergence must be explained by a near tie of that call, and
+    the GPU is then resynchronised."""
     cfg = BatchConfig(L=6, n_samples=2, n_temps=4, n_replicas=2, n_res=3)
     gpu, mir = make(cfg, seed=44)
-    gpu.prethermalize(30)
-    mir.sweep(0, 30, pretherm=True)
-    g, o = gpu_spins(gpu), mir.spins()
-    if not np.array_equal(g, o):
-        pytest.skip("near tie during pre-thermalisation (rare)")
-    np.testing.assert_array_equal(gpu.energies.cpu().numpy(), mir.energies())
+    for it in range(30):
+        gpu.prethermalize(1)
+        ties = mir.sweep(0, 1, pretherm=True)
+        g, o = gpu_spins(gpu), mir.spins()
+        if not np.array_equal(g, o):
+            assert_explained(cfg.L, g, o, ties, it)
+            resync(gpu, mir)
+        else:
+            np.testing.assert_array_equal(gpu.energies.cpu().numpy(), mir.energies())
+    record_ties(mir)
+    assert gpu.poll(10000) == 0
+
+
+def test_prethermalisation_continues_the_sweep_index():
+    """Two pre-thermalisation calls of n sweeps equal one call of 2n (fresh
+    random numbers, no replay), and a reset restarts the index."""
+    cfg = BatchConfig(L=6, n_samples=2, n_temps=4, n_replicas=2, n_res=3)
+    J = W.gaussian_couplings(6, 2, 45)
+    seeds = W.sample_seeds(W.SEED_BASE + 45, 2)
+    a = Batch(cfg, couplings=J, seeds=seeds)
+    b = Batch(cfg, couplings=J, seeds=seeds)
+    a.prethermalize(10)
+    a.prethermalize(10)
+    b.prethermalize(20)
+    np.testing.assert_array_equal(gpu_spins(a), gpu_spins(b))
+    c = Batch(cfg, couplings=J, seeds=seeds)
+    c.prethermalize(10)
+    c.reset_samples(0, 2, seeds=seeds, couplings=J, pretherm_sweeps=10)
+    d = Batch(cfg, couplings=J, seeds=seeds)
+    d.prethermalize(10)
+    np.testing.assert_array_equal(gpu_spins(c), gpu_spins(d))
+    assert not np.array_equal(gpu_spins(a), gpu_spins(d))
 
 
 # ----------------------------------------------------------------------------- statistics
@@ -522,9 +576,8 @@ def test_chaos_accumulators_match_oracle():
         gpu.houdayer()
         gpu.swap(True, True)
         gpu.measure(chaos=True)
-        mir.emcs()
-        if not np.array_equal(gpu_spins(gpu), mir.spins()):
-            pytest.skip("near tie changed the trajectory (rare)")
+        ties, pt_ties = mir.emcs()
+        diverged = diverged_samples(gpu, mir)
         for s, smp in enumerate(mir.samples):
             for k in range(cfg.n_temps):
                 for p in range(cfg.n_replicas // 2):
@@ -533,7 +586,15 @@ def test_chaos_accumulators_match_oracle():
                     bb = smp.spins[smp.lattice_at(2 * p + 1, k)]
                     q = O.pair_observables(cfg.L, smp.J, a, bb, 1.0)[0]
                     ref[s, k, 1] += q * q
-    np.testing.assert_array_equal(gpu.chaos.cpu().numpy(), ref)
+        if diverged:
+            # a near tie changed a trajectory: only that sample may differ;
+            # continue from the oracle's state and accumulators
+            assert diverged <= {s for s, _ in ties} | set(pt_ties)
+            resync(gpu, mir)
+            gpu.obs.copy_(torch.from_numpy(np.stack([s.obs for s in mir.samples])))
+            gpu.chaos.copy_(torch.from_numpy(ref))
+        np.testing.assert_array_equal(gpu.chaos.cpu().numpy(), ref)
+    record_ties(mir)
 
 
 def test_schedule_autotuner_reports_cluster_share():
@@ -544,3 +605,11 @@ def test_schedule_autotuner_reports_cluster_share():
     assert k in (1, 4) and len(table) == 2
     assert all(0.0 <= r["cluster_share"] < 1.0 for r in table)
     assert table[1]["cluster_ms_per_emcs"] < table[0]["cluster_ms_per_emcs"]
+
+
+def test_pooled_near_tie_rate():
+    """Near ties over every sweep-parity run of this module stay below 1e-5
+    of the local decisions (the tolerance on FP32 vs FP64 accept decisions)."""
+    if TIE_LEDGER["decisions"] == 0:
+        pytest.skip("no parity run recorded in this session")
+    assert TIE_LEDGER["ties"] < TIE_RATE_MAX * TIE_LEDGER["decisions"], TIE_LEDGER

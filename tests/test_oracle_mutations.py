@@ -38,6 +38,11 @@ MUTANTS = [
      "for (int ph = 0; ph < 1; ph++) {\n        for (int k = ph; k + 1 < n_temps; k += 2) {"),
     ("q^2 enumeration drops the square", "for (int b = 0; b < V; b++) q2 += C[a][b] * C[a][b];",
      "for (int b = 0; b < V; b++) q2 += C[a][b];"),
+    ("e^2 accumulated as e", "o[2] += e * e;", "o[2] += e;"),
+    ("q^4 accumulated as q^3", "o[7] += r[0] * r[0] * r[0] * r[0];", "o[7] += r[0] * r[0] * r[0];"),
+    ("overlap accumulated as |q|", "o[3] += r[0];", "o[3] += fabs(r[0]);"),
+    ("temperature grid divided by N_T", "(t_max - t_min) / (double)(n_temps - 1);",
+     "(t_max - t_min) / (double)(n_temps);"),
 ]
 
 

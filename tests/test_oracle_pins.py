@@ -5,6 +5,7 @@ a published value, a closed form, an invariant, a library routine or an exact
 enumeration.  They run on the CPU only.
 """
 import os
+from fractions import Fraction
 
 import numpy as np
 import pytest
@@ -390,7 +391,61 @@ def test_pair_observables_closed_forms():
     assert q == -1.0 and ql == 1.0
 
 
+# ----------------------------------------------------------------------------- temperature grid
+
+@pytest.mark.parametrize("n_temps,t_min,t_max", [(12, 0.2, 1.6), (16, 0.2, 1.6), (24, 0.2, 1.6),
+                                                 (32, 0.2, 1.6), (24, 0.42, 1.8), (60, 0.2, 2.0),
+                                                 (7, 0.35, 2.0), (2, 0.5, 1.5)])
+def test_temperature_grid_is_uniform_with_both_ends(n_temps, t_min, t_max):
+    """App. A.2: N_T temperatures uniformly spaced between T_min and T_max,
+    both included.  Checked against exact rational arithmetic on the two
+    binary64 end points: T_0 is T_min exactly, every T_k lies within the
+    rounding error of four IEEE operations (3 ulps of T_max) of
+    T_min + k (T_max - T_min)/(N_T - 1), so T_{N_T-1} is T_max and the
+    spacing is uniform to that precision; 1/T_k is the correctly rounded
+    reciprocal."""
+    T, beta = O.temperatures(n_temps, t_min, t_max)
+    a, b = Fraction(t_min), Fraction(t_max)
+    assert T[0] == t_min
+    for k in range(n_temps):
+        exact = a + k * (b - a) / (n_temps - 1)
+        assert abs(Fraction(float(T[k])) - exact) <= 3 * Fraction(np.spacing(t_max))
+        assert Fraction(float(beta[k])) == Fraction(float(1 / Fraction(float(T[k]))))
+    assert abs(T[-1] - t_max) <= 3 * np.spacing(t_max)
+    step = (t_max - t_min) / (n_temps - 1)
+    np.testing.assert_allclose(np.diff(T), step, rtol=0, atol=8 * np.spacing(t_max))
+
+
 # ----------------------------------------------------------------------------- the chain vs exact enumeration
+
+_SPINS_2x2x2 = np.where((np.arange(256)[:, None] >> np.arange(8)) & 1, -1, 1).astype(np.float64)
+
+
+def exact_pair_moments(J, T):
+    """<q^2> and <q^4> of two independent replicas on 2x2x2 (Eqs. (2)-(3)):
+    q(a, b) = (1/V) sum_i s^a_i s^b_i summed over all 65536 pair states with
+    the product of the two Boltzmann weights from the enumeration."""
+    _, P = O.enumerate_l2(J, T, want_probs=True)
+    Q = _SPINS_2x2x2 @ _SPINS_2x2x2.T / 8.0
+    q2 = np.array([p @ (Q ** 2) @ p for p in P])
+    q4 = np.array([p @ (Q ** 4) @ p for p in P])
+    return q2, q4
+
+
+def test_pair_moments_enumeration_agrees_with_the_enumerator():
+    """The pair-state sum for <q^2> equals the enumerator's
+    (1/V^2) sum_ij <s_i s_j>^2: two different routes to the same number."""
+    J = _rand_J(2, 19, grid=False)
+    q2, q4 = exact_pair_moments(J, T_GRID)
+    np.testing.assert_allclose(q2, O.enumerate_l2(J, T_GRID)[:, 1], rtol=1e-12)
+    assert np.all(q4 <= q2 + 1e-15) and np.all(q4 >= q2 ** 2 - 1e-15)   # q^2 <= 1; Jensen
+
+
+# accumulator columns of the chain (per temperature): (name, obs column,
+# divisor per measurement: 4 groups or 2 pairs)
+_CHAIN_COLS = (("e", 1, 4), ("e2", 2, 4), ("q", 3, 2), ("q2", 4, 2), ("ql", 5, 2), ("S", 6, 2),
+               ("q4", 7, 2))
+
 
 def _chain_vs_exact(rule, order, cluster, er_on, n_blocks=20, block=800, seed=5):
     L = 2
@@ -406,13 +461,15 @@ def _chain_vs_exact(rule, order, cluster, er_on, n_blocks=20, block=800, seed=5)
         before = smp.obs.copy()
         smp.emcs(block)
         d = smp.obs - before
-        n = d[:, 0:1]
-        means.append(np.stack([d[:, 1] / (n[:, 0] * 4), d[:, 4] / (n[:, 0] * 2),
-                               d[:, 5] / (n[:, 0] * 2), d[:, 6] / (n[:, 0] * 2)], 1))
+        n = d[:, 0]
+        means.append(np.stack([d[:, col] / (n * div) for _, col, div in _CHAIN_COLS], 1))
     means = np.array(means)
     est = means.mean(0)
     err = means.std(0, ddof=1) / np.sqrt(n_blocks)
-    exact = O.enumerate_l2(J, T)[:, [0, 1, 2, 3]]
+    ex = O.enumerate_l2(J, T)
+    q2, q4 = exact_pair_moments(J, T)
+    # Z2 symmetry (Sec. 2): <q> = 0 for every sample
+    exact = np.stack([ex[:, 0], ex[:, 4], np.zeros(len(T)), q2, ex[:, 2], ex[:, 3], q4], 1)
     z = np.abs(est - exact) / np.maximum(err, 1e-9)
     return z, smp
 
@@ -425,10 +482,11 @@ def _chain_vs_exact(rule, order, cluster, er_on, n_blocks=20, block=800, seed=5)
 ])
 def test_pthr_chain_reproduces_exact_averages_on_2x2x2(rule, order, cluster, er_on):
     """The full EMCS (sweeps, cluster move, PT, ER) samples the Boltzmann
-    weight at every temperature: <e>, <q^2>, <q_l>, <S> agree with exact
-    enumeration within 5 standard errors (20 blocks)."""
+    weight at every temperature: every accumulator -- <e>, <e^2>, <q>,
+    <q^2>, <q_l>, <S>, <q^4> -- agrees with exact enumeration (<q> = 0 by
+    symmetry) within 5 standard errors (20 blocks)."""
     z, smp = _chain_vs_exact(rule, order, cluster, er_on)
-    assert np.all(z < 5.0), z
+    assert np.all(z < 5.0), dict(zip([c[0] for c in _CHAIN_COLS], z.T))
     assert smp.pt_accepted.sum() > 0
     if er_on:
         assert smp.round_trips.sum() > 0

@@ -48,7 +48,7 @@ def trajectory_stats(cfg, n_emcs, seed):
     for _ in range(n_emcs):
         gpu.emcs(1)
         ties, pt_ties = mir.emcs()
-        near_ties += sum(len(v) for v in ties.values()) + pt_ties
+        near_ties += sum(len(v) for v in ties.values()) + sum(pt_ties.values())
         g = gpu.export_spins().cpu().numpy()
         if not (np.array_equal(g, mir.spins()) and np.array_equal(gpu.perm.cpu().numpy(), mir.perms())):
             diverged += 1
