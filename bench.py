@@ -35,6 +35,7 @@ sys.path.insert(0, ROOT)
 import workloads as W  # noqa: E402
 
 METRIC = "spin updates/ns and PTHR sweeps/s at L=16 (FP32 batched vs plain)"
+METRIC_OTHER = "spin updates/ns and PTHR sweeps/s at L={L} (FP32 batched vs plain)"
 UNIT = "spin-updates/ns"
 WL = W.WORKLOADS["c4"]      # the headline workload; --workload selects another for reports
 # Algorithmic ALU work of one Metropolis spin update: a
@@ -47,6 +48,11 @@ OPS_PER_UPDATE = 29
 # 4-site word of the site and its 6 neighbours are read and the site word is
 # written once per 4 updates (8 x 4 B / 4).
 SMEM_BYTES_PER_UPDATE = 8
+# instruction counts of the sweep kernel measured by ncu (per spin update) and
+# its DRAM traffic, valid for the kernel source they were taken on
+COUNTERS = os.path.join(ROOT, "profiles", "sweep_kernel_L16_counters.json")
+PEAK_NAMES = ("smem_read_Bps", "l2_read_Bps", "alu_inst_per_s", "fma_inst_per_s", "fma2_inst_per_s",
+              "fp64_inst_per_s")
 
 
 def peaks():
@@ -111,6 +117,36 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
+def measure_peaks(dev):
+    """On-device microbenchmarks (libpthr.so, pthr_measure_peak): shared-memory
+    and L2 load bandwidth and the issue rates of the ALU, FMA, f32x2 and FP64
+    pipes, each one timed launch over every SM."""
+    import ctypes
+    import torch
+    from paper_2605_25872_gb300 import _lib
+    lib = _lib.load()
+    scratch = torch.empty((4096 + (16 << 20),), dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    out = {}
+    for kind, name in enumerate(PEAK_NAMES):
+        rate, sec = ctypes.c_double(0.0), ctypes.c_double(0.0)
+        _lib.check(lib.pthr_measure_peak(kind, ctypes.c_void_p(scratch.data_ptr()), scratch.numel(),
+                                         ctypes.c_void_p(stream.cuda_stream), ctypes.byref(rate),
+                                         ctypes.byref(sec)))
+        out[name] = rate.value
+    del scratch
+    return out
+
+
+def kernel_counters():
+    """ncu counters of the sweep kernel, if they were taken on this source."""
+    if not os.path.exists(COUNTERS) or WL is not W.WORKLOADS["c4"]:
+        return None
+    with open(COUNTERS) as f:
+        c = json.load(f)
+    return c if c.get("kernel_version") == kernel_version() else None
+
+
 def batch_config(n_samples=None):
     from paper_2605_25872_gb300 import BatchConfig
     return BatchConfig(L=WL.L, n_samples=n_samples or WL.n_samples, n_temps=WL.n_temps,
@@ -151,12 +187,16 @@ def oracle_sample_run(n_threads, n_emcs=1, seed_offset=0):
     return (pt + res) * n_emcs, dt, used
 
 
-def cpu_baseline():
+def cpu_baseline(target_s=12.0):
+    """The oracle on every host core, one sample per thread, sized to about
+    target_s seconds of CPU work (a one-EMCS probe sets the EMCS count)."""
     cores = os.cpu_count() or 1
-    upd, dt, used = oracle_sample_run(cores)
+    _, dt1, _ = oracle_sample_run(cores)
+    n = max(1, min(5000, int(round(target_s / max(dt1, 1e-4)))))
+    upd, dt, used = oracle_sample_run(cores, n_emcs=n, seed_offset=1)
     return {"value": upd / (dt * 1e9), "unit": UNIT, "cores": used, "kind": "oracle",
-            "sample": f"{used} samples x 1 EMCS of the L={WL.L} workload (one sample per host thread), "
-                      f"{upd:.3g} spin updates in {dt:.1f} s"}
+            "sample": f"{used} samples x {n} EMCS of the L={WL.L} workload (one sample per host "
+                      f"thread), {upd:.3g} spin updates in {dt:.3g} s"}
 
 
 def run_reference(args):
@@ -184,15 +224,21 @@ def run_reference(args):
 
 
 def config_dict():
+    res = (f" + {WL.n_res} reservoir clones/group" if WL.er_on else "")
+    emcs = (f"{WL.sweeps_per_emcs} sweep{'s' if WL.sweeps_per_emcs > 1 else ''} + ACU(T<1) + PT"
+            + (f" + ER ({WL.res_sweeps_per_emcs} reservoir sweeps)" if WL.er_on else ""))
+    lat = WL.n_samples * WL.lattices_per_sample
+    lat_bytes = 2 * WL.L * WL.L * ((WL.L // 2 + 3) // 4) * 4
+    state_mb = (lat * lat_bytes + WL.n_samples * 3 * WL.V * 4) / 1e6
     return {"workload": f"{WL.name} (L={WL.L}, {WL.n_samples} samples x {WL.n_temps} T "
-                        f"[{WL.t_min},{WL.t_max}] x {WL.n_replicas} replicas + {WL.n_res} reservoir "
-                        f"clones/group; EMCS = {WL.sweeps_per_emcs} sweeps + ACU(T<1) + PT + ER "
-                        f"({WL.res_sweeps_per_emcs} reservoir sweeps))",
+                        f"[{WL.t_min},{WL.t_max}] x {WL.n_replicas} replicas{res}; EMCS = {emcs})",
             "L": WL.L, "n_samples": WL.n_samples, "n_temps": WL.n_temps, "n_replicas": WL.n_replicas,
-            "n_res": WL.n_res, "sweeps_per_emcs": WL.sweeps_per_emcs,
-            "res_sweeps_per_emcs": WL.res_sweeps_per_emcs, "update_rule": "metropolis",
-            "couplings": "N(0,1) on the 2^-18 grid (seeded)",
-            "l2": "inputs larger than L2: 330 MB of resident state per GPU"}
+            "n_res": WL.n_res if WL.er_on else 0, "sweeps_per_emcs": WL.sweeps_per_emcs,
+            "res_sweeps_per_emcs": WL.res_sweeps_per_emcs if WL.er_on else 0,
+            "update_rule": "metropolis", "couplings": "N(0,1) on the 2^-18 grid (seeded)",
+            "l2": (f"inputs larger than L2: {state_mb:.0f} MB of spins and couplings resident per GPU"
+                   if state_mb > 129 else
+                   f"{state_mb:.0f} MB of spins and couplings resident per GPU (fits in the 129 MB L2)")}
 
 
 # ----------------------------------------------------------------------------- GPU arm
@@ -228,7 +274,8 @@ def run_gpu(args):
     pt_upd, res_upd = updates_per_emcs(S)
     upd = pt_upd + res_upd
 
-    # ---- warm-up
+    # ---- on-chip peaks of this GPU (rank 0), then warm-up
+    measured = measure_peaks(dev) if (rank == 0 and not args.no_extras) else None
     for _ in range(args.warmup):
         b.emcs(1)
     stream.synchronize()
@@ -297,22 +344,52 @@ def run_gpu(args):
     result = None
     if rank == 0:
         pk, pk_kind = peaks()
-        sm_max = float(pk.get("sm_max_mhz", 2070.0))
         n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
-        alu_peak = n_sm * 128 * sm_max * 1e6 / 1e12                # T lane-ops/s
-        achieved_ops = OPS_PER_UPDATE * upd / (ms_sweep * 1e-3) / 1e12
-        smem_peak = n_sm * 128 * sm_max * 1e6 / 1e12                # TB/s (128 B/clk/SM)
-        achieved_smem = SMEM_BYTES_PER_UPDATE * upd / (ms_sweep * 1e-3) / 1e12
-        traffic = None
-        tr_path = os.path.join(ROOT, "profiles", "sweep_kernel_L16_traffic.json")
-        if os.path.exists(tr_path) and WL is W.WORKLOADS["c4"]:
-            with open(tr_path) as f:
-                tr = json.load(f)
-            if tr.get("kernel_version") == kernel_version():
-                traffic = tr.get("dram_bytes_per_launch")
+        mhz = clocks.get("sm_mhz") or float(pk.get("sm_max_mhz", 2070.0))
+        upd_per_s = upd / (ms_sweep * 1e-3)
+        # issue roofline of the sweep kernel: thread-instructions per update
+        # (ncu) x updates/s over 128 thread-instructions/clk/SM at the median
+        # SM clock of the timed region
+        issue_peak = n_sm * 128 * mhz * 1e6 / 1e12                    # T thread-instr/s
+        cnt = kernel_counters()
+        inst = cnt["inst_per_update"] if cnt else None
+        traffic = cnt.get("dram_bytes_per_launch") if cnt else None
+        achieved_inst = (inst * upd_per_s / 1e12) if inst else None
+        alg = OPS_PER_UPDATE * upd_per_s / 1e12
+        smem_achieved = SMEM_BYTES_PER_UPDATE * upd_per_s
+        roof = {"kernel": f"sweep_kernel<{WL.L}, Metropolis>", "bound": "alu",
+                "achieved": achieved_inst if inst else alg, "peak": issue_peak,
+                "unit": "T thread-instr/s",
+                "frac": (achieved_inst if inst else alg) / issue_peak, "traffic": traffic,
+                "basis": (f"ncu: {inst:.2f} thread-instructions per spin update (all pipes) x "
+                          f"updates/s in the sweep launch (CUDA events), over {n_sm} SMs x 128 "
+                          f"thread-instr/clk x {mhz:.0f} MHz (median SM clock of the timed region)")
+                if inst else (f"no ncu counters for this kernel source: algorithmic {OPS_PER_UPDATE} "
+                              f"ALU ops per update over {n_sm} SMs x 128 lanes x {mhz:.0f} MHz"),
+                "algorithmic_ops_per_update": OPS_PER_UPDATE,
+                "algorithmic_frac": alg / issue_peak}
+        if measured:
+            if cnt and cnt.get("alu_inst_per_update"):
+                a = cnt["alu_inst_per_update"] * upd_per_s
+                roof["alu_pipe"] = {"achieved": a / 1e12, "peak": measured["alu_inst_per_s"] / 1e12,
+                                    "unit": "T thread-instr/s", "frac": a / measured["alu_inst_per_s"],
+                                    "inst_per_update": cnt["alu_inst_per_update"],
+                                    "peak_basis": "measured lop3 issue rate (pthr_measure_peak)"}
+            roof["smem"] = {"achieved_TBps": smem_achieved / 1e12,
+                            "peak_TBps": measured["smem_read_Bps"] / 1e12,
+                            "frac": smem_achieved / measured["smem_read_Bps"],
+                            "bytes_per_update": SMEM_BYTES_PER_UPDATE,
+                            "peak_basis": "measured 16-byte shared loads (pthr_measure_peak)",
+                            "target_half_of_smem_roofline_met": smem_achieved >= 0.5 * measured["smem_read_Bps"]}
+            roof["l2_peak_TBps"] = measured["l2_read_Bps"] / 1e12
         pairs = S * (WL.n_replicas // 2) * n_acu_temps()
+        ms_cluster = float(phase[:, 1].mean())
         plain = plain_form(dev, upd / S, seeds, J)
         e2e = end_to_end(dev, cfg, J, seeds, args.steps)
+        serving = None
+        if WL is W.WORKLOADS["c4"] and world == 1:
+            serving = serve_measure(args.serve_budget, args.serve_requests, args.serve_mem_gb,
+                                    args.serve_max_slots, args.serve_chunk)
         result = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
@@ -323,19 +400,14 @@ def run_gpu(args):
             "updates_per_ns_graph": world * upd / (ms_graph * 1e6),
             "pt_updates_per_emcs": pt_upd, "res_updates_per_emcs": res_upd,
             "houdayer_pair_moves_per_s": world * pairs * 1e3 / ms_step,
-            "phase_ms": {"sweep": ms_sweep, "houdayer": float(phase[:, 1].mean()),
+            "sites_labelled_per_ns": pairs * WL.V / (ms_cluster * 1e6) if ms_cluster > 0 else None,
+            "phase_ms": {"sweep": ms_sweep, "houdayer": ms_cluster,
                          "swap": float(phase[:, 2].mean()), "measure": float(phase[:, 3].mean())},
             "plain": plain,
-            "roofline": {"kernel": f"sweep_kernel<{WL.L}, Metropolis>", "bound": "alu",
-                         "achieved": achieved_ops, "peak": alu_peak, "unit": "Tops/s",
-                         "frac": achieved_ops / alu_peak, "traffic": traffic,
-                         "ops_per_update": OPS_PER_UPDATE,
-                         "peak_basis": f"{n_sm} SMs x 128 FP32/INT32 lanes x {sm_max:.0f} MHz "
-                                       f"(sm_max_mhz, {pk_kind})",
-                         "smem": {"achieved_TBps": achieved_smem, "peak_TBps": smem_peak,
-                                  "frac": achieved_smem / smem_peak,
-                                  "bytes_per_update": SMEM_BYTES_PER_UPDATE}},
+            "roofline": roof,
+            "measured_peaks": {k: v for k, v in measured.items()} if measured else None,
             "gpu_launches": 4 * args.steps,
+            "serving": serving,
             "cpu_baseline": cpu_baseline(),
             "e2e": e2e,
             "clocks": clocks,
@@ -418,26 +490,24 @@ def end_to_end(dev, cfg, J, seeds, steps):
                         f"{steps} EMCS, D2H observables after every EMCS"}
 
 
-def run_serve(args):
+def serve_measure(budget, n_req, mem_gb, max_slots, max_chunk):
     """Serving: Poisson stream of single-sample requests with L uniform in
     {6, 8, 10, 12, 16} (24 temperatures 0.2..1.6, 4 replicas + 4 reservoir
     clones, paper EMCS), admitted into per-L resident pools sized from a
-    device-memory budget; rate = 0.8 x the measured capacity."""
+    device-memory budget; rate = 0.8 x the measured capacity.  Returns the
+    p50/p99 time from arrival to a finished budget and the aggregate spin
+    updates/ns over the run."""
     import torch
-    from paper_2605_25872_gb300.build import build
     from paper_2605_25872_gb300 import required_bytes, BatchConfig
     from paper_2605_25872_gb300.serve import PoolSpec, Request, Server
-    build()
-    torch.cuda.set_device(0)
-    budget = args.serve_budget
-    mem = args.serve_mem_gb * 1e9
+    mem = mem_gb * 1e9
     specs = []
     for L in W.SERVE_SIZES:
         one = required_bytes(BatchConfig(L=L, n_samples=1, n_temps=24))
-        slots = int(min(args.serve_max_slots, (mem / len(W.SERVE_SIZES)) // one))
+        slots = int(min(max_slots, (mem / len(W.SERVE_SIZES)) // one))
         specs.append(PoolSpec(L=L, slots=slots, n_temps=24))
-    # capacity probe: every pool full, EMCS steps timed with all pools in flight
-    srv = Server(specs, use_group=args.serve_group)
+    # capacity probe: every pool full, EMCS timed with all pools in flight
+    srv = Server(specs, max_chunk=max_chunk)
     probe = [Request(rid=-1 - i * 100000 - k, L=sp.L, seed=10 ** 6 + i * 100000 + k, budget_emcs=10 ** 6)
              for i, sp in enumerate(specs) for k in range(sp.slots)]
     per_emcs_s = srv.fill_and_time(probe, 5)
@@ -445,22 +515,31 @@ def run_serve(args):
     torch.cuda.synchronize()
     cap = min(sp.slots / (budget * per_emcs_s) for sp in specs) * len(specs)   # requests/s
     lam = 0.8 * cap
-    n_req = args.serve_requests
     times, Ls = W.poisson_arrivals(n_req, lam, W.batch_seed(5))
     reqs = [Request(rid=i, L=int(Ls[i]), seed=W.batch_seed(5) + 7919 * i, budget_emcs=budget,
                     arrival=float(times[i])) for i in range(n_req)]
-    srv = Server(specs, use_group=args.serve_group)
+    srv = Server(specs, max_chunk=max_chunk)
     srv.run(reqs, realtime=True)
     st = srv.stats()
-    line = {"mode": "serve", "metric": "time-to-budget p50/p99 and aggregate spin updates/ns",
+    return {"metric": "time-to-budget p50/p99 and aggregate spin updates/ns",
             "p50_s": st["p50_s"], "p99_s": st["p99_s"], "updates_per_ns": st["updates_per_ns"],
             "requests": st["requests"], "budget_emcs": budget, "lambda_per_s": lam,
-            "capacity_per_s": cap, "full_pool_emcs_s": per_emcs_s, "slots": {sp.L: sp.slots for sp in specs},
-            "memory_budget_gb": args.serve_mem_gb, "emcs_steps": st["emcs_steps"],
-            "group_graph": bool(args.serve_group),
+            "capacity_per_s": cap, "full_pool_emcs_s": per_emcs_s,
+            "slots": {sp.L: sp.slots for sp in specs}, "memory_budget_gb": mem_gb,
+            "emcs_steps": st["emcs_steps"], "chunks": st["chunks"], "max_chunk": max_chunk,
             "config": {"workload": "serving: L uniform in {6,8,10,12,16}, 24 T 0.2..1.6, 4 replicas + "
                                    "4 reservoir clones, paper EMCS, couplings drawn on the device from each "
-                                   "request's seed, 960-sweep reservoir pre-thermalisation at admission"}}
+                                   "request's seed, 960-sweep reservoir pre-thermalisation at admission, "
+                                   "Poisson arrivals at 0.8 x the measured capacity"}}
+
+
+def run_serve(args):
+    import torch
+    from paper_2605_25872_gb300.build import build
+    build()
+    torch.cuda.set_device(0)
+    line = {"mode": "serve", **serve_measure(args.serve_budget, args.serve_requests, args.serve_mem_gb,
+                                             args.serve_max_slots, args.serve_chunk)}
     print(json.dumps(line))
     return 0
 
@@ -492,14 +571,16 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=200)
     ap.add_argument("--serve-mem-gb", type=float, default=2.0)
     ap.add_argument("--serve-max-slots", type=int, default=128)
-    ap.add_argument("--serve-group", action="store_true",
-                    help="advance all pools with one group graph per EMCS (admissions then "
-                         "delay every pool, so per-pool stepping is the default)")
+    ap.add_argument("--serve-chunk", type=int, default=64,
+                    help="most EMCS a pool runs between two host checks (serving)")
     ap.add_argument("--autotune", action="store_true", help="print the shape sweep for the workload")
     ap.add_argument("--workload", default="c4", choices=["c2", "c3", "c4"],
                     help="c4 (L=16 PTHR, the headline) or the batched L=8 / L=12 workloads")
     args = ap.parse_args()
     WL = W.WORKLOADS[args.workload]
+    if args.workload != "c4":
+        global METRIC
+        METRIC = METRIC_OTHER.format(L=WL.L)
     if args.samples == W.WORKLOADS["c4"].n_samples:
         args.samples = WL.n_samples
     if args.serve:

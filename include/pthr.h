@@ -16,7 +16,8 @@
  *    managed) memory of the current device; "host" pointers are CPU memory.
  *  - The library allocates no device memory of its own: the caller allocates
  *    one device workspace of pthr_required_bytes() bytes and keeps it alive
- *    until pthr_destroy().  The library never frees it.
+ *    until pthr_destroy().  The library never frees it.  Each sub-buffer is
+ *    followed by a 256-byte guard block (pthr_check_canaries).
  *  - Every call is asynchronous on the CUDA stream given at creation (or by
  *    pthr_set_stream) and returns as soon as its kernels are enqueued.
  *    Errors found on the host (bad arguments) return PTHR_E_INVAL at once;
@@ -285,6 +286,38 @@ PTHR_API void pthr_group_destroy(pthr_group *g);
  * blob saved from a batch with the same configuration. */
 PTHR_API pthr_status pthr_save(pthr_batch *b, void *blob, size_t *bytes);
 PTHR_API pthr_status pthr_load(pthr_batch *b, const void *blob, size_t bytes);
+
+/* Spin autocorrelation of the reservoir clones at T_max (Sec. 3, ER: the
+ * residence of 960 sweeps is set by C(960) < 1e-3, with
+ * C(tau) = (1/V) sum_i <s_i(t) s_i(t + tau)> from an equilibrium start at
+ * T_max).  For the samples [first, first+count): the current configuration
+ * of every reservoir clone is copied to the snapshot, then n_points times
+ * sweeps_per_point reservoir sweeps at T_max are run (the
+ * pre-thermalisation sweeps of pthr_prethermalize_reservoir, which continue
+ * the sample's PRETH sweep index) and after the p-th block
+ * out_device[s - first][p] (int64, device) receives
+ *   sum over the sample's n_replicas * n_res reservoir clones and V sites of
+ *   s_i(snapshot) s_i(now),
+ * an exact integer: C(tau = (p+1) sweeps_per_point) = out / (n_replicas *
+ * n_res * V) for that sample.  The reservoir clones keep the extra sweeps
+ * (a stationary evolution at T_max).  snapshot_device: caller-owned device
+ * scratch, 16-byte aligned, at least count * n_replicas * n_res *
+ * pthr_lattice_bytes(L) bytes (else PTHR_E_NOMEM); its contents are not
+ * needed afterwards.  Needs n_res >= 1 and an EMCS boundary (PTHR_E_STATE).
+ * Asynchronous. */
+PTHR_API pthr_status pthr_reservoir_autocorrelation(pthr_batch *b, int first, int count, int n_points,
+                                                    int sweeps_per_point, void *snapshot_device,
+                                                    size_t snapshot_bytes, int64_t *out_device);
+
+/* Guard check: every workspace sub-buffer is followed by a 256-byte guard
+ * block written with a fixed pattern at creation (included in
+ * pthr_required_bytes).  Synchronises the stream and compares every guard
+ * block; returns PTHR_OK if all are intact, else PTHR_E_BOUNDS with
+ * *bad_buffer (if not NULL) set to the PTHR_BUF_* index of the first
+ * sub-buffer whose guard was overwritten (-1 when all are intact).  A
+ * debugging aid for out-of-range writes; pthr_load restores the guards
+ * from the blob. */
+PTHR_API pthr_status pthr_check_canaries(pthr_batch *b, int *bad_buffer);
 
 /* Description of the last error on this handle (never NULL). */
 PTHR_API const char *pthr_last_error(const pthr_batch *b);

@@ -249,8 +249,10 @@ class OracleSample:
             for r in range(self.n_res):
                 lat = g * self.nslot + int(self.perm[g * self.nslot + self.n_temps + r])
                 for sw in range(n_sweeps):
-                    sweep(self.L, self.J, self.spins[lat], self.beta[-1], self.seed, lat,
-                          PRETHERM_EMCS, self.pretherm_done + sw, self.cfg.order, self.cfg.rule)
+                    _, ties, _ = sweep(self.L, self.J, self.spins[lat], self.beta[-1], self.seed, lat,
+                                       PRETHERM_EMCS, self.pretherm_done + sw, self.cfg.order,
+                                       self.cfg.rule, tie_eps=self.cfg.tie_eps)
+                    self.n_ties[0] += len(ties)
                 self.E_lat[lat] = energy(self.L, self.J, self.spins[lat])
         self.pretherm_done += n_sweeps
 

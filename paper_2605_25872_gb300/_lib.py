@@ -32,7 +32,9 @@ EXPORTS = ("pthr_required_bytes", "pthr_buffer_info", "pthr_lattice_bytes", "pth
            "pthr_houdayer", "pthr_cluster_labels", "pthr_swap", "pthr_observables", "pthr_emcs",
            "pthr_prethermalize_reservoir", "pthr_poll", "pthr_export_spins", "pthr_import_spins",
            "pthr_reset_samples", "pthr_set_active", "pthr_save", "pthr_load", "pthr_last_error",
-           "pthr_version", "pthr_group_create", "pthr_group_emcs", "pthr_group_destroy")
+           "pthr_version", "pthr_group_create", "pthr_group_emcs", "pthr_group_destroy",
+           "pthr_measure_peak", "pthr_check_canaries", "pthr_reservoir_autocorrelation")
+PEAK_SMEM_READ, PEAK_L2_READ, PEAK_ALU, PEAK_FMA, PEAK_FMA2, PEAK_FP64 = range(6)
 
 
 class Config(ctypes.Structure):
@@ -60,11 +62,14 @@ class PthrError(RuntimeError):
 _lib = None
 
 
-def load(path: str = LIB_PATH):
-    """Load libpthr.so; raise if it is missing (no fallback path exists)."""
+def load(path: str | None = None):
+    """Load libpthr.so; raise if it is missing (no fallback path exists).
+    PTHR_LIBRARY in the environment names another build of the same library
+    (the range-checked debug build)."""
     global _lib
     if _lib is not None:
         return _lib
+    path = path or os.environ.get("PTHR_LIBRARY") or LIB_PATH
     if not os.path.exists(path):
         raise ImportError(f"PTHR CUDA library not built: {path} is missing "
                           f"(run paper_2605_25872_gb300.build.build())")
@@ -95,6 +100,9 @@ def load(path: str = LIB_PATH):
         "pthr_load": [vp, vp, sz],
         "pthr_group_create": [vp, i, vp, P(vp)],
         "pthr_group_emcs": [vp, i],
+        "pthr_measure_peak": [i, vp, sz, vp, P(ctypes.c_double), P(ctypes.c_double)],
+        "pthr_check_canaries": [vp, P(ctypes.c_int)],
+        "pthr_reservoir_autocorrelation": [vp, i, i, i, i, vp, sz, vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)

@@ -6,7 +6,9 @@ of arXiv 2605.25872 computed from the accumulators that the GPU kernels fill.
 - temperature random-walk time tau_TRW = N_r N_T EMCS / round trips (Sec. 5);
 - chaotic parameter X_{T1,T2} = <q^2_{T1,T2}> / sqrt(<q^2_{T1,T1}> <q^2_{T2,T2}>)
   (Sec. 5);
-- effective dynamic exponent z_eff from two sizes (Sec. 5).
+- effective dynamic exponent z_eff from two sizes (Sec. 5);
+- the T_max spin autocorrelation C(tau) that sets the reservoir residence
+  (Sec. 3, ER).
 """
 from __future__ import annotations
 
@@ -95,3 +97,14 @@ def run_binned(batch, t_max: int, n_bins: int, chaos: bool = False):
         if t in ends:
             out[ends[t]] = (batch.obs.cpu().numpy().copy(), batch.chaos.cpu().numpy().copy())
     return out
+
+
+def spin_autocorrelation(sums, n_replicas: int, n_res: int, V: int):
+    """C(tau) = (1/V) sum_i <s_i(t) s_i(t + tau)> (Sec. 3, ER) from the
+    integer sums of pthr_reservoir_autocorrelation, out[sample, point]:
+    returns (per-sample C [S, n_points], disorder average [n_points], its
+    standard error [n_points])."""
+    c = np.asarray(sums, dtype=np.float64) / float(n_replicas * n_res * V)
+    n = c.shape[0]
+    err = c.std(axis=0, ddof=1) / np.sqrt(n) if n > 1 else np.full(c.shape[1], np.nan)
+    return c, c.mean(axis=0), err

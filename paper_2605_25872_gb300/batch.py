@@ -6,6 +6,7 @@ sub-buffer) and the CUDA stream; every operation is a call into libpthr.so.
 from __future__ import annotations
 
 import ctypes
+import weakref
 from dataclasses import dataclass
 
 import numpy as np
@@ -15,6 +16,7 @@ from . import _lib
 from ._lib import check
 
 RULES = {"metropolis": _lib.METROPOLIS, "heatbath": _lib.HEATBATH}
+LIVE = weakref.WeakSet()      # open batches (the tests check their guard blocks)
 CLUSTERS = {"off": _lib.CLUSTER_OFF, "acu": _lib.CLUSTER_ACU, "single": _lib.CLUSTER_SINGLE}
 
 
@@ -109,6 +111,7 @@ class Batch:
         self.h = h
         self.stream.synchronize()
         self._views = {}
+        LIVE.add(self)
         if tuning:
             self.set_tuning(**tuning)
 
@@ -276,6 +279,36 @@ class Batch:
     def load(self, blob: bytes):
         check(self.lib.pthr_load(self.h, ctypes.c_char_p(blob), len(blob)), self.h)
 
+    def reservoir_autocorrelation(self, n_points: int, sweeps_per_point: int, first: int = 0,
+                                  count: int | None = None) -> torch.Tensor:
+        """Integer sums of s_i(t) s_i(t + tau) over every reservoir clone and
+        site of each sample, tau = sweeps_per_point, 2 sweeps_per_point, ...
+        (pthr_reservoir_autocorrelation); device int64 [count, n_points]."""
+        c = self.cfg
+        count = c.n_samples - first if count is None else count
+        nbytes = count * c.n_replicas * c.n_res * self.lattice_bytes()
+        snap = torch.empty(max(nbytes, 16), dtype=torch.uint8, device=self.device)
+        out = torch.zeros((count, n_points), dtype=torch.int64, device=self.device)
+        check(self.lib.pthr_reservoir_autocorrelation(self.h, first, count, n_points, sweeps_per_point,
+                                                      ctypes.c_void_p(snap.data_ptr()), snap.numel(),
+                                                      ctypes.c_void_p(out.data_ptr())), self.h)
+        self.stream.synchronize()
+        return out
+
+    def lattice_bytes(self) -> int:
+        n = ctypes.c_size_t(0)
+        check(self.lib.pthr_lattice_bytes(self.cfg.L, ctypes.byref(n)))
+        return n.value
+
+    def check_canaries(self) -> int:
+        """-1 if every guard block after a workspace sub-buffer is intact,
+        else the PTHR_BUF_* index of the first overwritten one."""
+        bad = ctypes.c_int(-1)
+        st = self.lib.pthr_check_canaries(self.h, ctypes.byref(bad))
+        if st not in (_lib.PTHR_OK, _lib.PTHR_E_BOUNDS):
+            check(st, self.h)
+        return bad.value
+
     def synchronize(self):
         self.stream.synchronize()
 
@@ -308,6 +341,36 @@ class Group:
 
     def emcs(self, n: int = 1):
         check(self.lib.pthr_group_emcs(self.h, n))
+
+    def reservoir_autocorrelation(self, n_points: int, sweeps_per_point: int, first: int = 0,
+                                  count: int | None = None) -> torch.Tensor:
+        """Integer sums of s_i(t) s_i(t + tau) over every reservoir clone and
+        site of each sample, tau = sweeps_per_point, 2 sweeps_per_point, ...
+        (pthr_reservoir_autocorrelation); device int64 [count, n_points]."""
+        c = self.cfg
+        count = c.n_samples - first if count is None else count
+        nbytes = count * c.n_replicas * c.n_res * self.lattice_bytes()
+        snap = torch.empty(max(nbytes, 16), dtype=torch.uint8, device=self.device)
+        out = torch.zeros((count, n_points), dtype=torch.int64, device=self.device)
+        check(self.lib.pthr_reservoir_autocorrelation(self.h, first, count, n_points, sweeps_per_point,
+                                                      ctypes.c_void_p(snap.data_ptr()), snap.numel(),
+                                                      ctypes.c_void_p(out.data_ptr())), self.h)
+        self.stream.synchronize()
+        return out
+
+    def lattice_bytes(self) -> int:
+        n = ctypes.c_size_t(0)
+        check(self.lib.pthr_lattice_bytes(self.cfg.L, ctypes.byref(n)))
+        return n.value
+
+    def check_canaries(self) -> int:
+        """-1 if every guard block after a workspace sub-buffer is intact,
+        else the PTHR_BUF_* index of the first overwritten one."""
+        bad = ctypes.c_int(-1)
+        st = self.lib.pthr_check_canaries(self.h, ctypes.byref(bad))
+        if st not in (_lib.PTHR_OK, _lib.PTHR_E_BOUNDS):
+            check(st, self.h)
+        return bad.value
 
     def synchronize(self):
         self.stream.synchronize()

@@ -96,9 +96,16 @@ pthr_status check_config(const pthr_config *c) {
     return PTHR_OK;
 }
 
+// Every sub-buffer starts on a 256-byte boundary and is followed by a
+// 256-byte guard block filled with CANARY at creation; pthr_check_canaries
+// finds any write that ran past the end of a sub-buffer.
+constexpr size_t GUARD_BYTES = 256;
+constexpr unsigned char CANARY = 0xC5;
+
 struct Layout {
     size_t off[PTHR_NBUF];
     size_t len[PTHR_NBUF];
+    size_t guard[PTHR_NBUF];   // offset of the guard block after each sub-buffer
     size_t total;
 };
 
@@ -130,6 +137,8 @@ Layout make_layout(const pthr_config *c) {
     for (int i = 0; i < PTHR_NBUF; ++i) {
         l.off[i] = o;
         o += (l.len[i] + 255) & ~(size_t)255;
+        l.guard[i] = o;
+        o += GUARD_BYTES;
     }
     l.total = o;
     return l;
@@ -372,6 +381,8 @@ PTHR_API pthr_status pthr_create_batch(const pthr_config *cfg, void *device_work
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);   // hs is pageable and freed below
     delete[] hs;
     if (e == cudaSuccess) e = cudaMemsetAsync(d.status, 0, 16, b->stream);
+    for (int i = 0; i < PTHR_NBUF && e == cudaSuccess; ++i)
+        e = cudaMemsetAsync(base + l.guard[i], CANARY, GUARD_BYTES, b->stream);
     if (e == cudaSuccess) {
         // tables: one IEEE-rounded division each, the same bits as the
         // per-use divisions they replace
@@ -743,5 +754,65 @@ PTHR_API void pthr_group_destroy(pthr_group *g) {
 }
 
 PTHR_API const char *pthr_last_error(const pthr_batch *b) { return b ? b->err : g_err; }
+
+PTHR_API pthr_status pthr_reservoir_autocorrelation(pthr_batch *b, int first, int count, int n_points,
+                                                    int sweeps_per_point, void *snapshot_device,
+                                                    size_t snapshot_bytes, int64_t *out_device) {
+    if (!b) return fail(nullptr, PTHR_E_INVAL, "NULL handle");
+    if (b->cfg.n_res < 1) return fail(b, PTHR_E_INVAL, "the batch has no reservoir clones");
+    if (first < 0 || count < 1 || first + count > b->cfg.n_samples || n_points < 1 || sweeps_per_point < 1 ||
+        (long long)n_points * sweeps_per_point >= (1LL << 23) || !snapshot_device || !out_device)
+        return fail(b, PTHR_E_INVAL, "bad sample range, point count, sweeps or NULL buffer");
+    if (((uintptr_t)snapshot_device) & 15) return fail(b, PTHR_E_INVAL, "snapshot must be 16-byte aligned");
+    const size_t need = (size_t)count * b->cfg.n_replicas * b->cfg.n_res * (size_t)lattice_words(b->cfg.L) * 4;
+    if (snapshot_bytes < need)
+        return fail(b, PTHR_E_NOMEM, "snapshot needs %zu bytes, got %zu", need, snapshot_bytes);
+    if (b->pt_sweep_off || b->res_sweep_off)
+        return fail(b, PTHR_E_STATE, "call at an EMCS boundary");
+    uint32_t *snap = (uint32_t *)snapshot_device;
+    CUDA_TRY(b, launch_snapshot_reservoir(b->dev, first, count, snap, b->stream), "snapshot");
+    for (int p = 0; p < n_points; ++p) {
+        pthr_status st = do_sweep(b, 0, sweeps_per_point, first, count, 1);
+        if (st != PTHR_OK) return st;
+        CUDA_TRY(b, launch_reservoir_overlap(b->dev, first, count, snap, (long long *)out_device, n_points, p,
+                                             b->stream), "overlap");
+    }
+    return PTHR_OK;
+}
+
+PTHR_API pthr_status pthr_check_canaries(pthr_batch *b, int *bad_buffer) {
+    if (!b) return fail(nullptr, PTHR_E_INVAL, "NULL handle");
+    const Layout l = make_layout(&b->cfg);
+    std::vector<unsigned char> h(GUARD_BYTES * PTHR_NBUF);
+    const unsigned char *base = (const unsigned char *)b->ws;
+    for (int i = 0; i < PTHR_NBUF; ++i)
+        CUDA_TRY(b, cudaMemcpyAsync(h.data() + i * GUARD_BYTES, base + l.guard[i], GUARD_BYTES,
+                                    cudaMemcpyDeviceToHost, b->stream), "guard copy");
+    CUDA_TRY(b, cudaStreamSynchronize(b->stream), "guard sync");
+    if (bad_buffer) *bad_buffer = -1;
+    for (int i = 0; i < PTHR_NBUF; ++i)
+        for (size_t k = 0; k < GUARD_BYTES; ++k)
+            if (h[i * GUARD_BYTES + k] != CANARY) {
+                if (bad_buffer) *bad_buffer = i;
+                return fail(b, PTHR_E_BOUNDS, "guard block after workspace buffer %d was overwritten", i);
+            }
+    return PTHR_OK;
+}
+
+PTHR_API pthr_status pthr_measure_peak(int kind, void *scratch_device, size_t scratch_bytes, void *stream,
+                                       double *rate, double *seconds) {
+    if (kind < 0 || kind >= PTHR_NPEAK || !rate || !seconds)
+        return fail(nullptr, PTHR_E_INVAL, "bad peak kind or NULL output");
+    if (!scratch_device || scratch_bytes < (size_t)PEAK_SINK_BYTES ||
+        (kind == PTHR_PEAK_L2_READ && scratch_bytes < (size_t)PEAK_SINK_BYTES + (1u << 20)))
+        return fail(nullptr, PTHR_E_INVAL, "scratch buffer too small (%zu bytes)", scratch_bytes);
+    double work = 0.0;
+    float ms = 0.f;
+    cudaError_t e = run_peak(kind, scratch_device, scratch_bytes, (cudaStream_t)stream, &work, &ms);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "peak microbenchmark");
+    *seconds = ms * 1e-3;
+    *rate = ms > 0.f ? work / (ms * 1e-3) : 0.0;
+    return PTHR_OK;
+}
 
 }  // extern "C"

@@ -25,10 +25,14 @@ namespace pthr {
 
 namespace {
 
-__device__ __forceinline__ int find_root(volatile int *parent, int x, int cap, bool &ok) {
+__device__ __forceinline__ int find_root(volatile int *parent, int x, int cap, bool &ok,
+                                         uint32_t *status = nullptr, int V = 0) {
     for (int it = 0; it < cap; ++it) {
         const int p = parent[x];
         if (p == x) return x;
+#ifdef PTHR_DEBUG
+        if (!PTHR_DCHECK(status, p >= 0 && p < V && parent[p] >= 0 && parent[p] < V)) { ok = false; return x; }
+#endif
         const int gp = parent[p];
         if (gp != p) parent[x] = gp;   // path halving: gp is an ancestor of x
         x = gp;
@@ -37,10 +41,11 @@ __device__ __forceinline__ int find_root(volatile int *parent, int x, int cap, b
     return x;
 }
 
-__device__ __forceinline__ void unite(volatile int *parent, int a, int b, int cap, bool &ok) {
+__device__ __forceinline__ void unite(volatile int *parent, int a, int b, int cap, bool &ok,
+                                      uint32_t *status = nullptr, int V = 0) {
     for (int it = 0; it < cap; ++it) {
-        a = find_root(parent, a, cap, ok);
-        b = find_root(parent, b, cap, ok);
+        a = find_root(parent, a, cap, ok, status, V);
+        b = find_root(parent, b, cap, ok, status, V);
         if (!ok || a == b) return;
         if (a < b) { const int t = a; a = b; b = t; }   // hook the larger root a under b
         const int old = atomicCAS(const_cast<int *>(&parent[a]), a, b);
@@ -168,6 +173,7 @@ __global__ void __launch_bounds__(512, 4) cluster_kernel(ClusterArgs a) {
     const int k = t % n_acu; t /= n_acu;
     const int P = t % b.NPAIR; t /= b.NPAIR;
     const int s = a.sample_first + t;
+    if (!PTHR_DCHECK(b.status, s >= 0 && s < b.S && k < b.NT && P < b.NPAIR)) return;
     if (!b.active[s]) return;
     const uint32_t emcs = b.emcs[s];
     if (!a.label_only && (emcs % (uint32_t)b.acu_interval) != 0u) return;
@@ -176,6 +182,8 @@ __global__ void __launch_bounds__(512, 4) cluster_kernel(ClusterArgs a) {
     const int ga = 2 * P, gb = 2 * P + 1;
     const int la = ga * b.NSLOT + b.perm[((size_t)s * b.NR + ga) * b.NSLOT + k];
     const int lb = gb * b.NSLOT + b.perm[((size_t)s * b.NR + gb) * b.NSLOT + k];
+    if (!PTHR_DCHECK(b.status, la >= ga * b.NSLOT && la < (ga + 1) * b.NSLOT &&
+                                lb >= gb * b.NSLOT && lb < (gb + 1) * b.NSLOT && gb < b.NR)) return;
     const uint32_t pair_id = (uint32_t)(P * b.NT + k);
     uint32_t *ga_ptr = b.spins + ((size_t)s * b.NLAT + la) * LW;
     uint32_t *gb_ptr = b.spins + ((size_t)s * b.NLAT + lb) * LW;
@@ -244,12 +252,12 @@ __global__ void __launch_bounds__(512, 4) cluster_kernel(ClusterArgs a) {
         while (C) {
             const int x = __ffs(C) - 1;
             C &= C - 1u;
-            unite(vp, L * r + x, L * r2 + x, cap, ok);
+            unite(vp, L * r + x, L * r2 + x, cap, ok, b.status, V);
         }
     }
     __syncthreads();
     for (int i = tid; i < V; i += T) {
-        const int r = find_root(vp, i, cap, ok);
+        const int r = find_root(vp, i, cap, ok, b.status, V);
         parent[i] = r;
     }
     if (!ok) s_ok = 0;

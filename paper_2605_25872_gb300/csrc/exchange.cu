@@ -28,7 +28,11 @@ __global__ void swap_kernel(Batch b, int flags, int first) {
         int *perm = s_perm + g * b.NSLOT;
         double *Ep = s_E + g * b.NSLOT;
         int32_t *gperm = b.perm + ((size_t)s * b.NR + g) * b.NSLOT;
-        for (int i = lane; i < b.NSLOT; i += 32) perm[i] = gperm[i];
+        for (int i = lane; i < b.NSLOT; i += 32) {
+            int v = gperm[i];
+            if (!PTHR_DCHECK(b.status, v >= 0 && v < b.NSLOT)) v = i;
+            perm[i] = v;
+        }
         __syncwarp();
         for (int i = lane; i < b.NT; i += 32) Ep[i] = b.E[(size_t)s * b.NLAT + g * b.NSLOT + perm[i]];
         __syncwarp();
@@ -127,6 +131,7 @@ __global__ void __launch_bounds__(32 * MEASURE_WARPS) measure_kernel(Batch b, in
     const int item = blockIdx.x * MEASURE_WARPS + (threadIdx.x >> 5);
     if (item >= count * b.NT) return;                 // warp-uniform
     const int s = first + item / b.NT, k = item % b.NT;
+    if (!PTHR_DCHECK(b.status, s >= 0 && s < b.S)) return;
     if (!b.active[s]) return;
     const int32_t *perm = b.perm + (size_t)s * b.NR * b.NSLOT;
     const uint32_t *spins = b.spins + (size_t)s * b.NLAT * LW;
@@ -134,6 +139,8 @@ __global__ void __launch_bounds__(32 * MEASURE_WARPS) measure_kernel(Batch b, in
     for (int P = 0; P < b.NPAIR; ++P) {
         const int la = 2 * P * b.NSLOT + perm[2 * P * b.NSLOT + k];
         const int lb = (2 * P + 1) * b.NSLOT + perm[(2 * P + 1) * b.NSLOT + k];
+        if (!PTHR_DCHECK(b.status, la >= 2 * P * b.NSLOT && la < (2 * P + 1) * b.NSLOT &&
+                                    lb >= (2 * P + 1) * b.NSLOT && lb < (2 * P + 2) * b.NSLOT)) return;
         int nneg, ndiff, cneg = 0;
         overlap_counts<L>(spins + (size_t)la * LW, spins + (size_t)lb * LW, lane, 32, nneg, ndiff);
         if (chaos) {
@@ -159,6 +166,9 @@ __global__ void __launch_bounds__(32 * MEASURE_WARPS) measure_kernel(Batch b, in
     if (lane < b.NPAIR) {
         const double Tk = b.tabT[k];
         const int la = 2 * lane * b.NSLOT + perm[2 * lane * b.NSLOT + k];
+        if (!PTHR_DCHECK(b.status, tn >= 0 && tn <= V && td >= 0 && td <= 3 * V && tc >= 0 && tc <= V)) {
+            tn = 0; td = 0; tc = 0;
+        }
         q = b.tabQ[tn];
         ql = b.tabQl[td];
         const double Ha = b.E[(size_t)s * b.NLAT + la];

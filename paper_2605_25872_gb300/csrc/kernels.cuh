@@ -2,6 +2,7 @@
 #pragma once
 
 #include "pthr_internal.cuh"
+#include "pthr_peaks.h"
 
 namespace pthr {
 
@@ -45,5 +46,14 @@ cudaError_t launch_init_state(const Batch &b, int first, int count, cudaStream_t
 cudaError_t launch_advance_pretherm(const Batch &b, int first, int count, int n_sweeps, cudaStream_t st);
 cudaError_t launch_export_spins(const Batch &b, int8_t *out, cudaStream_t st);
 cudaError_t launch_import_spins(const Batch &b, const int8_t *in, cudaStream_t st);
+
+// autocorr.cu
+cudaError_t launch_snapshot_reservoir(const Batch &b, int first, int count, uint32_t *snap, cudaStream_t st);
+cudaError_t launch_reservoir_overlap(const Batch &b, int first, int count, const uint32_t *snap,
+                                     long long *out, int n_points, int point, cudaStream_t st);
+
+// peaks.cu
+constexpr int PEAK_SINK_BYTES = 4096;   // scratch words the microbenchmarks may store to
+cudaError_t run_peak(int kind, void *scratch, size_t scratch_bytes, cudaStream_t st, double *work, float *ms);
 
 }  // namespace pthr

@@ -180,6 +180,16 @@ __device__ __forceinline__ void set_status(uint32_t *status, uint32_t bit) {
     atomicOr(status, bit);
 }
 
+// Range checks of the debug build (PTHR_DEBUG, the stand-in for a memory
+// sanitizer): a failed check latches STATUS_BOUNDS and evaluates to false,
+// and the caller then skips or clamps the access, so nothing outside a
+// buffer is read or written.  Release builds compile every check away.
+#ifdef PTHR_DEBUG
+#define PTHR_DCHECK(status, cond) ((cond) ? true : (::pthr::set_status((status), ::pthr::STATUS_BOUNDS), false))
+#else
+#define PTHR_DCHECK(status, cond) true
+#endif
+
 // Supported linear sizes (template instantiations).
 #define PTHR_FOR_EACH_L(X) X(2) X(4) X(6) X(8) X(10) X(12) X(14) X(16) X(18) X(20) X(22) X(24)
 

@@ -267,6 +267,7 @@ sweep_kernel(SweepArgs a) {
         if (!a.do_pt) return;
         s = a.sample_first + t / a.pt_tasks; chunk = t % a.pt_tasks; kind = 0;
     }
+    if (!PTHR_DCHECK(b.status, s >= 0 && s < b.S)) return;
     if (!b.active[s]) return;
     const int per = kind ? b.NRES : b.NT;
     const int total = b.NR * per;
@@ -274,6 +275,7 @@ sweep_kernel(SweepArgs a) {
     const int e0 = chunk * Kmax;
     const int K = min(Kmax, total - e0);
     if (K <= 0) return;
+    if (!PTHR_DCHECK(b.status, K <= MAXK)) return;
     const int nsw = kind ? a.n_res_sweeps : a.n_pt_sweeps;
     int sweep_base = kind ? a.res_sweep_base : a.pt_sweep_base;
     if (a.emcs_override) {
@@ -306,7 +308,8 @@ sweep_kernel(SweepArgs a) {
     if (tid < K) {
         const int e = e0 + tid;
         const int g = e / per, pos = kind ? b.NT + (e % per) : (e % per);
-        const int clone = b.perm[((size_t)s * b.NR + g) * b.NSLOT + pos];
+        int clone = b.perm[((size_t)s * b.NR + g) * b.NSLOT + pos];
+        if (!PTHR_DCHECK(b.status, g < b.NR && clone >= 0 && clone < b.NSLOT)) clone = 0;
         s_lat[tid] = g * b.NSLOT + clone;
         // round 1 of every sweep draw of this lattice starts from M0 times
         // its round-0 word 0, which depends on the lattice and the block only
@@ -445,6 +448,17 @@ sweep_kernel(SweepArgs a) {
             for (int gi = 0; gi < GP; ++gi) {
                 const int g = g0 + gi * Gt;
                 const GroupGeo q = ONE_G ? (c ? qc1 : qc0) : group_geo<L>(g, c);
+#ifdef PTHR_DEBUG
+                {
+                    const int cm = ((c ^ 1) * ROWS + ROWS - 1) * W + W - 1;
+                    const bool in = g < G && q.own >= 0 && q.own < LW && q.xa >= 0 && q.xa < LW &&
+                                    q.wA >= 0 && q.wA < LW && q.wB >= 0 && q.wB < LW && q.yp >= 0 &&
+                                    q.yp < LW && q.ym >= 0 && q.ym < LW && q.zp >= 0 && q.zp < LW &&
+                                    q.zm >= 0 && q.zm < LW && 4 * q.own + 3 < LB && 4 * cm + 3 < LB &&
+                                    kbase + KT <= MAXK;
+                    if (!PTHR_DCHECK(b.status, in)) continue;
+                }
+#endif
                 uint32_t ahi, alo;
                 mul_wide(0xD2511F53u, (uint32_t)g, ahi, alo);
                 const SweepRng rng = sweep_rng(ahi, alo, rng_elo, c3, rk0, rk1);

@@ -4,9 +4,10 @@ A request is one disorder sample (couplings, seed, lattice size L) that needs
 a fixed budget of EMCS.  The server keeps one resident batch ("pool") per
 lattice size, each on its own CUDA stream.  It admits waiting requests into
 free slots whenever a slot frees up (by device memory: the pools are sized
-from a memory budget).  It advances every pool that has work by one EMCS at
-a time, so pools overlap on the device.  It reads a request's observables
-back when its budget is done, then frees the slot.
+from a memory budget).  It advances every pool that has work in chunks of
+EMCS that end exactly when the next request of that pool finishes, so pools
+overlap on the device and the host meets a pool once per chunk.  It reads a
+request's observables back when its budget is done, then frees the slot.
 
 Because every random number is keyed by the request's own seed and
 EMCS counter, a request's result is the same whether it runs alone or in a
@@ -75,7 +76,7 @@ class GpuPool:
         self.batch = Batch(self.cfg, device=device, stream=self.stream)
         self.batch.set_active(0, spec.slots, False)
         self.graph = graph
-        self.host_obs = np.zeros((spec.slots, spec.n_temps, 8))
+        self.event = torch.cuda.Event()
 
     def reset(self, slot, req: Request):
         self.reset_many([slot], [req])
@@ -106,40 +107,57 @@ class GpuPool:
             run.append(i)
         flush()
 
-    def step(self):
-        self.batch.emcs(1, graph=self.graph)
+    def step(self, n=1):
+        """Enqueue n EMCS of every active slot; returns at once."""
+        self.batch.emcs(n, graph=self.graph)
+        self.event.record(self.stream)
+
+    def ready(self):
+        return self.event.query()
 
     def wait(self):
         self.stream.synchronize()
 
     def read(self, slot):
-        obs = self.batch.obs[slot].cpu().numpy().copy()
-        trips = self.batch.round_trips[slot].cpu().numpy().copy()
+        with torch_stream(self.stream):
+            obs = self.batch.obs[slot].cpu().numpy().copy()
+            trips = self.batch.round_trips[slot].cpu().numpy().copy()
         return obs, trips
 
     def free(self, slot):
         self.batch.set_active(slot, 1, False)
 
 
+def torch_stream(stream):
+    import torch
+    return torch.cuda.stream(stream)
+
+
 class Server:
-    """Admission queue -> slots -> EMCS steps -> completion -> readback.
+    """Admission queue -> slots -> chunks of EMCS -> completion -> readback.
 
-    With use_group=True (GPU pools) all pools advance by one CUDA-graph launch
-    per EMCS (pthr_group), each pool on its own stream inside the graph."""
+    Each pool advances in chunks: k EMCS enqueued at once on its stream, k
+    the smallest remaining budget among its busy slots (at most max_chunk),
+    so no request runs past its budget and the host meets the device once
+    per chunk rather than once per EMCS.  While a chunk runs the host admits
+    arrivals into free slots (stream-ordered after the chunk) and services
+    the pools whose chunk has finished; pools on different streams overlap
+    on the device."""
 
-    def __init__(self, specs, pool_factory=None, clock=None, use_group=False):
+    def __init__(self, specs, pool_factory=None, clock=None, max_chunk=64):
         self.specs = {s.L: s for s in specs}
         self.pool_factory = pool_factory or (lambda spec: GpuPool(spec))
-        self.use_group = use_group
-        self.group = None
+        self.max_chunk = max(1, int(max_chunk))
         self.pools = {L: self.pool_factory(s) for L, s in self.specs.items()}
         self.slot_req = {L: [None] * s.slots for L, s in self.specs.items()}
         self.remaining = {L: np.zeros(s.slots, dtype=np.int64) for L, s in self.specs.items()}
+        self.in_flight = {L: False for L in self.specs}
         self.queue = {L: deque() for L in self.specs}
         self.done = []
         self.clock = clock or time.perf_counter
         self.t0 = None
         self.emcs_steps = {L: 0 for L in self.specs}
+        self.chunks = {L: 0 for L in self.specs}
 
     def now(self):
         return self.clock() - self.t0
@@ -149,73 +167,80 @@ class Server:
             raise ValueError(f"no pool for L={req.L}")
         self.queue[req.L].append(req)
 
-    def _admit(self):
-        for L, q in self.queue.items():
-            slots = self.slot_req[L]
-            free = [i for i, r in enumerate(slots) if r is None]
-            take = []
-            while q and free:
-                take.append((free.pop(0), q.popleft()))
-            if not take:
-                continue
-            pool = self.pools[L]
-            if hasattr(pool, "reset_many"):
-                pool.reset_many([s for s, _ in take], [r for _, r in take])
-            else:
-                for s, r in take:
-                    pool.reset(s, r)
-            t = self.now()
-            for slot, req in take:
-                req.admitted = t
-                slots[slot] = req
-                self.remaining[L][slot] = req.budget_emcs
+    def _admit(self, L):
+        q = self.queue[L]
+        slots = self.slot_req[L]
+        free = [i for i, r in enumerate(slots) if r is None]
+        take = []
+        while q and free:
+            take.append((free.pop(0), q.popleft()))
+        if not take:
+            return
+        pool = self.pools[L]
+        if hasattr(pool, "reset_many"):
+            pool.reset_many([s for s, _ in take], [r for _, r in take])
+        else:
+            for s, r in take:
+                pool.reset(s, r)
+        t = self.now()
+        for slot, req in take:
+            req.admitted = t
+            slots[slot] = req
+            self.remaining[L][slot] = req.budget_emcs
+
+    def _complete(self, L):
+        """Read back and free the slots whose budget is done (pool L idle)."""
+        pool, rem = self.pools[L], self.remaining[L]
+        for slot, req in enumerate(self.slot_req[L]):
+            if req is not None and rem[slot] == 0:
+                req.obs, req.round_trips = pool.read(slot)
+                req.finished = self.now()
+                pool.free(slot)
+                self.slot_req[L][slot] = None
+                self.done.append(req)
+
+    def _enqueue_chunk(self, L):
+        rem = self.remaining[L]
+        busy = [slot for slot, r in enumerate(self.slot_req[L]) if r is not None]
+        if not busy:
+            self.in_flight[L] = False
+            return
+        k = int(min(self.max_chunk, min(rem[s] for s in busy)))
+        self.pools[L].step(k)
+        for s in busy:
+            rem[s] -= k
+        self.in_flight[L] = True
+        self.emcs_steps[L] += k
+        self.chunks[L] += 1
+
+    def _service(self, L):
+        """Pool L has no chunk in flight: complete, admit, enqueue the next."""
+        self._complete(L)
+        self._admit(L)
+        self._enqueue_chunk(L)
 
     def fill_and_time(self, requests, n_emcs):
         """Capacity probe: admit `requests` (filling the pools), then time
-        n_emcs steps of every busy pool (admission excluded)."""
+        n_emcs EMCS of every busy pool, all pools in flight together
+        (admission excluded).  Returns seconds per full-pool EMCS."""
         self.t0 = self.clock()
         for r in requests:
             self.submit(r)
-        self._admit()
+        for L in self.pools:
+            self._admit(L)
         for p in self.pools.values():
             p.wait()
         t0 = self.clock()
-        for _ in range(n_emcs):
-            self._step_all()
+        for L, p in self.pools.items():
+            if any(r is not None for r in self.slot_req[L]):
+                p.step(n_emcs)
+        for p in self.pools.values():
+            p.wait()
         return (self.clock() - t0) / n_emcs
 
     def busy(self):
-        return any(r is not None for sl in self.slot_req.values() for r in sl)
-
-    def _step_all(self):
-        stepped = [L for L, sl in self.slot_req.items() if any(r is not None for r in sl)]
-        if self.use_group:
-            from .batch import Group
-            if self.group is None:
-                self.group = Group([p.batch for p in self.pools.values()])
-            for p in self.pools.values():          # admissions on the pool streams first
-                self.group.stream.wait_stream(p.stream)
-            self.group.emcs(1)                     # every pool, one graph launch
-            self.group.synchronize()
-            for L in stepped:
-                self.emcs_steps[L] += 1
-        else:
-            for L in stepped:                 # enqueue one EMCS per busy pool (streams overlap)
-                self.pools[L].step()
-                self.emcs_steps[L] += 1
-        for L in stepped:
-            self.pools[L].wait()
-            rem = self.remaining[L]
-            for slot, req in enumerate(self.slot_req[L]):
-                if req is None:
-                    continue
-                rem[slot] -= 1
-                if rem[slot] == 0:
-                    req.obs, req.round_trips = self.pools[L].read(slot)
-                    req.finished = self.now()
-                    self.pools[L].free(slot)
-                    self.slot_req[L][slot] = None
-                    self.done.append(req)
+        return any(self.in_flight.values()) or any(
+            r is not None for sl in self.slot_req.values() for r in sl)
 
     def run(self, requests, realtime=True):
         """Serve `requests` (sorted by arrival).  With realtime=True arrivals
@@ -226,11 +251,20 @@ class Server:
             now = self.now()
             while pending and (not realtime or pending[0].arrival <= now):
                 self.submit(pending.popleft())
-            self._admit()
-            if self.busy():
-                self._step_all()
-            elif pending:
-                time.sleep(max(0.0, min(0.001, pending[0].arrival - self.now())))
+            progressed = False
+            for L, pool in self.pools.items():
+                if self.in_flight[L]:
+                    if not pool.ready():
+                        self._admit(L)          # into free slots, after the chunk
+                        continue
+                    self._service(L)
+                    progressed = True
+                elif self.queue[L] or any(r is not None for r in self.slot_req[L]):
+                    self._service(L)
+                    progressed = True
+            if not progressed:
+                nxt = pending[0].arrival - self.now() if (pending and realtime) else 0.0
+                time.sleep(max(0.0002, min(0.001, nxt)))
         return self.done
 
     def stats(self):
@@ -242,4 +276,4 @@ class Server:
                 "p99_s": float(np.percentile(lat, 99)) if len(lat) else None,
                 "makespan_s": span,
                 "updates_per_ns": upd / (span * 1e9) if span > 0 else None,
-                "emcs_steps": dict(self.emcs_steps)}
+                "emcs_steps": dict(self.emcs_steps), "chunks": dict(self.chunks)}

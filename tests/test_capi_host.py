@@ -89,3 +89,14 @@ def test_null_handle_calls_fail_cleanly(lib):
     assert lib.pthr_emcs(None, 1, 0) == _lib.PTHR_E_INVAL
     assert lib.pthr_poll(None, 0) == _lib.PTHR_E_INVAL
     lib.pthr_destroy(None)
+
+
+def test_measure_peak_rejects_bad_arguments_without_cuda(lib):
+    r, t = ctypes.c_double(), ctypes.c_double()
+    assert lib.pthr_measure_peak(99, ctypes.c_void_p(256), 1 << 20, None, ctypes.byref(r),
+                                 ctypes.byref(t)) == _lib.PTHR_E_INVAL
+    assert lib.pthr_measure_peak(_lib.PEAK_SMEM_READ, None, 1 << 20, None, ctypes.byref(r),
+                                 ctypes.byref(t)) == _lib.PTHR_E_INVAL
+    # the L2 benchmark needs at least 1 MB past the 4 KB of sink words
+    assert lib.pthr_measure_peak(_lib.PEAK_L2_READ, ctypes.c_void_p(256), 8192, None, ctypes.byref(r),
+                                 ctypes.byref(t)) == _lib.PTHR_E_INVAL

@@ -530,6 +530,67 @@ def test_status_word_reads_ok():
     assert b.poll(10000) == 0
 
 
+def test_reservoir_autocorrelation_matches_oracle():
+    """C(tau) at T_max (Sec. 3, ER): from a common state, the GPU's integer
+    sums of s_i(t) s_i(t + tau) over every reservoir clone equal the oracle's,
+    computed from its own snapshot and the same pre-thermalisation sweeps,
+    for every sample whose oracle sweeps met no near tie."""
+    cfg = BatchConfig(L=6, n_samples=4, n_temps=4, n_replicas=2, n_res=3)
+    gpu, mir = make(cfg, seed=52)
+    gpu.prethermalize(20)
+    mir.sweep(0, 20, pretherm=True)
+    resync(gpu, mir)                       # common starting point
+    n_points, per = 4, 5
+    got = gpu.reservoir_autocorrelation(n_points, per).cpu().numpy()
+    snap = [np.stack([smp.spins[smp.lattice_at(g, cfg.n_temps + r)] for g in range(cfg.n_replicas)
+                      for r in range(cfg.n_res)]).astype(np.int64) for smp in mir.samples]
+    ref = np.zeros((cfg.n_samples, n_points), dtype=np.int64)
+    tied = set()
+    for p in range(n_points):
+        ties = mir.sweep(0, per, pretherm=True)
+        tied |= {s for s, _ in ties}
+        for s, smp in enumerate(mir.samples):
+            now = np.stack([smp.spins[smp.lattice_at(g, cfg.n_temps + r)] for g in range(cfg.n_replicas)
+                            for r in range(cfg.n_res)]).astype(np.int64)
+            ref[s, p] = int((snap[s] * now).sum())
+    compared = [s for s in range(cfg.n_samples) if s not in tied]
+    assert len(compared) >= 3
+    np.testing.assert_array_equal(got[compared], ref[compared])
+    assert np.all(np.abs(ref) <= cfg.n_replicas * cfg.n_res * cfg.V)
+    assert gpu.poll(10000) == 0
+
+
+def test_poll_times_out_while_a_long_launch_runs():
+    """Failure detection on the host: pthr_poll(0) right after a long
+    reservoir pre-thermalisation is enqueued returns PTHR_E_TIMEOUT without
+    disturbing the stream; a later unbounded poll drains it and returns OK."""
+    from paper_2605_25872_gb300 import _lib
+    cfg = BatchConfig(L=16, n_samples=4, n_temps=4, n_replicas=2, n_res=4)
+    b = Batch(cfg, couplings=W.gaussian_couplings(16, 4, 9), seeds=W.sample_seeds(10, 4))
+    b.synchronize()
+    b.prethermalize(20000)
+    assert b.poll(0) == _lib.PTHR_E_TIMEOUT
+    assert b.poll(-1) == _lib.PTHR_OK
+    assert b.check_canaries() == -1
+
+
+def test_guard_blocks_catch_a_write_past_a_buffer():
+    """The guard block after a sub-buffer detects a write one byte past its
+    end (made from the host through the workspace tensor: no kernel writes
+    out of range)."""
+    from paper_2605_25872_gb300 import _lib, buffer_info
+    cfg = BatchConfig(L=6, n_samples=2, n_temps=4, n_replicas=2, n_res=1)
+    b = Batch(cfg)
+    assert b.check_canaries() == -1
+    off, n = buffer_info(cfg, _lib.BUF_ENERGY)
+    guard = off + ((n + 255) & ~255)
+    saved = b.ws[guard].clone()
+    b.ws[guard] = 0
+    assert b.check_canaries() == _lib.BUF_ENERGY
+    b.ws[guard] = saved
+    assert b.check_canaries() == -1
+
+
 def test_bounded_cluster_loop_reports_noconverge_without_changing_spins():
     """Failure detection without a fault: an iteration cap of 1 makes the
     union-find give up; the kernel latches PTHR_E_NOCONVERGE, returns, leaves

@@ -4,6 +4,7 @@ import numpy as np
 import pytest
 import torch
 
+import oracle as O
 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -33,13 +34,11 @@ def alone(spec, req):
     return b.obs[0].cpu().numpy(), b.round_trips[0].cpu().numpy()
 
 
-@pytest.mark.parametrize("use_group", [False, True])
-def test_serving_result_alone_equals_in_the_mix(use_group):
-    specs = [PoolSpec(L=6, slots=3, n_temps=8, sweeps_per_emcs=2, res_sweeps_per_emcs=6,
-                      pretherm_sweeps=12),
-             PoolSpec(L=8, slots=2, n_temps=8, sweeps_per_emcs=2, res_sweeps_per_emcs=6,
-                      pretherm_sweeps=12)]
-    srv = Server(specs, use_group=use_group)
+SPECS = [PoolSpec(L=6, slots=3, n_temps=8, sweeps_per_emcs=2, res_sweeps_per_emcs=6, pretherm_sweeps=12),
+         PoolSpec(L=8, slots=2, n_temps=8, sweeps_per_emcs=2, res_sweeps_per_emcs=6, pretherm_sweeps=12)]
+
+
+def mixed_requests():
     rng = np.random.default_rng(5)
     reqs = []
     for i in range(10):
@@ -47,7 +46,13 @@ def test_serving_result_alone_equals_in_the_mix(use_group):
         cpl = W.gaussian_couplings(L, 1, 500 + i)[0] if i % 3 else None
         reqs.append(Request(rid=i, L=L, seed=9000 + i, budget_emcs=int(rng.integers(3, 9)),
                             arrival=0.0, couplings=cpl))
-    done = srv.run(reqs, realtime=False)
+    return reqs
+
+
+@pytest.mark.parametrize("max_chunk", [1, 64])
+def test_serving_result_alone_equals_in_the_mix(max_chunk):
+    srv = Server(SPECS, max_chunk=max_chunk)
+    done = srv.run(mixed_requests(), realtime=False)
     assert len(done) == 10
     for r in done:
         spec = srv.specs[r.L]
@@ -56,6 +61,34 @@ def test_serving_result_alone_equals_in_the_mix(use_group):
         np.testing.assert_array_equal(r.round_trips, trips)
     st = srv.stats()
     assert st["p50_s"] > 0 and st["updates_per_ns"] > 0
+    if max_chunk > 1:
+        assert sum(st["chunks"].values()) < sum(st["emcs_steps"].values())
+
+
+def test_served_requests_match_the_oracle():
+    """Requests served in a busy mixed-L pool (admitted as slots free up,
+    advanced in chunks) against the FP64 oracle run on the same seed and
+    couplings: reservoir pre-thermalisation then the request's EMCS budget.
+    Every request whose oracle run met no near tie has bit-identical
+    observable accumulators and round-trip counts."""
+    srv = Server(SPECS, max_chunk=64)
+    done = srv.run(mixed_requests(), realtime=False)
+    compared = 0
+    for r in done:
+        if r.couplings is None:
+            continue            # couplings drawn on the device (checked in test_gpu_parity)
+        spec = srv.specs[r.L]
+        o = O.OracleSample(r.L, spec.n_temps, spec.t_min, spec.t_max, r.seed,
+                           J=r.couplings.astype(np.float64), n_groups=spec.n_replicas,
+                           n_res=spec.n_res, sweeps_per_emcs=spec.sweeps_per_emcs,
+                           res_sweeps_per_emcs=spec.res_sweeps_per_emcs)
+        o.prethermalize_reservoir(spec.pretherm_sweeps)
+        o.emcs(r.budget_emcs)
+        if o.n_ties.sum() == 0:
+            np.testing.assert_array_equal(r.obs, o.obs)
+            np.testing.assert_array_equal(r.round_trips, o.round_trips)
+            compared += 1
+    assert compared >= 3
 
 
 def test_group_graph_equals_separate_batches():

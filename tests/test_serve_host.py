@@ -22,9 +22,12 @@ class FakePool:
         self.active[slot] = True
         self.log.append(("reset", slot, req.rid))
 
-    def step(self):
-        self.emcs[self.active] += 1
-        self.log.append(("step", int(self.active.sum())))
+    def step(self, n=1):
+        self.emcs[self.active] += n
+        self.log.append(("step", int(self.active.sum()), n))
+
+    def ready(self):
+        return True
 
     def wait(self):
         pass
@@ -56,6 +59,20 @@ def test_requests_finish_with_their_budget_and_slots_are_reused():
             assert live <= pool.spec.slots + 10
     st = srv.stats()
     assert st["requests"] == 9 and st["p99_s"] >= st["p50_s"]
+
+
+def test_chunks_end_exactly_at_the_next_completion():
+    """A chunk never runs a request past its budget: chunk lengths are the
+    smallest remaining budget of the busy slots (at most max_chunk)."""
+    specs = [PoolSpec(L=6, slots=3)]
+    srv = Server(specs, pool_factory=FakePool, max_chunk=5)
+    reqs = [Request(rid=i, L=6, seed=i, budget_emcs=b) for i, b in enumerate((7, 3, 12, 4))]
+    done = srv.run(reqs, realtime=False)
+    for r in done:
+        assert r.obs[0][1] == r.budget_emcs
+    steps = [ev[2] for ev in srv.pools[6].log if ev[0] == "step"]
+    assert steps[0] == 3 and max(steps) <= 5
+    assert srv.stats()["chunks"][6] == len(steps) < sum(r.budget_emcs for r in reqs)
 
 
 def test_fifo_admission_per_lattice_size():
