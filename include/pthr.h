@@ -69,7 +69,13 @@ typedef enum {
                                 guarded was skipped, nothing was written)          */
 } pthr_status;
 
-enum { PTHR_METROPOLIS = 0, PTHR_HEATBATH = 1 };
+/* Local update rules (Sec. 3 item i).  PTHR_MICSA: microcanonical
+ * simulated annealing (App. A.1), one walker per (clone, 4-site group of the
+ * checkerboard, colour pass), drawn from the canonical distribution of a
+ * non-negative energy at the clone's temperature (E_w = -T ln u) when the
+ * pass reaches its group; a spin flips when the walker holds more than its
+ * Delta E, which is then taken from the walker. */
+enum { PTHR_METROPOLIS = 0, PTHR_HEATBATH = 1, PTHR_MICSA = 2 };
 enum { PTHR_CLUSTER_OFF = 0, PTHR_CLUSTER_ACU = 1, PTHR_CLUSTER_SINGLE = 2 };
 enum { PTHR_SWAP_PT = 1, PTHR_SWAP_ER = 2 };
 enum { PTHR_OBS_MEASURE = 1, PTHR_OBS_READ_HOST = 2, PTHR_OBS_READ_DEVICE = 4, PTHR_OBS_RESET = 8,
@@ -125,7 +131,7 @@ typedef struct {
     int sweeps_per_emcs;      /* local sweeps of PT clones per EMCS (paper: 10)      */
     int res_sweeps_per_emcs;  /* sweeps of each reservoir clone per EMCS (960/4)     */
     int acu_interval;         /* cluster move every acu_interval EMCS (>= 1)         */
-    int update_rule;          /* PTHR_METROPOLIS or PTHR_HEATBATH                    */
+    int update_rule;          /* PTHR_METROPOLIS, PTHR_HEATBATH or PTHR_MICSA        */
     int cluster_mode;         /* PTHR_CLUSTER_OFF / _ACU / _SINGLE                   */
     int er_on;                /* 1: entropic reservoir step on                       */
     int reserved;             /* must be 0                                           */

@@ -25,7 +25,7 @@ _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
 _lib = None
 _lock = threading.Lock()
 
-RULE_METROPOLIS, RULE_HEATBATH = 0, 1
+RULE_METROPOLIS, RULE_HEATBATH, RULE_MICSA = 0, 1, 2
 ORDER_CHECKERBOARD, ORDER_LEXICOGRAPHIC = 0, 1
 CLUSTER_OFF, CLUSTER_ACU, CLUSTER_SINGLE = 0, 1, 2
 PRETHERM_EMCS = 0xFFFFFFFF  # EMCS counter word used by reservoir pre-thermalisation
@@ -76,6 +76,10 @@ def lib():
             L.orc_init_spins.argtypes = [i, u64, i, vp]
             L.orc_sweep.argtypes = [i, vp, vp, d, u64, i, u32, u32, i, i, d, i, vp, i, vp, vp]
             L.orc_sweep.restype = ctypes.c_long
+            L.orc_sweep_micsa.argtypes = [i, vp, vp, d, u64, i, i, u32, u32, d, vp, i, vp, vp, vp]
+            L.orc_sweep_micsa.restype = ctypes.c_long
+            L.orc_micsa_walker.argtypes = [i, vp, d, d, vp, d, vp]
+            L.orc_micsa_walker.restype = d
             L.orc_cc_labels.argtypes = [i, vp, vp, vp]
             L.orc_cc_labels.restype = i
             L.orc_acu.argtypes = [i, vp, vp, u64, u32, u32, vp]
@@ -140,6 +144,31 @@ def sweep(L, J, s, beta, seed, lat, emcs, sweep_idx, order=ORDER_CHECKERBOARD,
                           sweep_idx, order, rule, tie_eps, int(field_err_bound), _p(ties),
                           max_ties, ctypes.byref(n_ties), ctypes.byref(dE))
     return acc, ties[:min(n_ties.value, max_ties)].copy(), dE.value
+
+
+def sweep_micsa(L, J, s, beta, seed, e, kind, emcs, sweep_idx, tie_eps=1e-6, max_ties=4096):
+    """One MicSA sweep in place (walkers keyed by the lattice's position e
+    within its kind).  Returns (accepted, sites a near tie may have changed,
+    dE, near-tie decisions)."""
+    J = np.ascontiguousarray(J, dtype=np.float64)
+    assert s.dtype == np.int8 and s.flags["C_CONTIGUOUS"]
+    ties = np.zeros(max_ties, dtype=np.int32)
+    n_sites, n_dec = ctypes.c_int(0), ctypes.c_int(0)
+    dE = ctypes.c_double(0.0)
+    acc = lib().orc_sweep_micsa(L, _p(J), _p(s), float(beta), seed, e, kind, emcs & 0xFFFFFFFF, sweep_idx,
+                                tie_eps, _p(ties), max_ties, ctypes.byref(n_sites), ctypes.byref(n_dec),
+                                ctypes.byref(dE))
+    return acc, ties[:min(n_sites.value, max_ties)].copy(), dE.value, n_dec.value
+
+
+def micsa_walker(dE, beta, u, tie_eps=1e-6):
+    """The walker rule on the sites with energy changes dE (in order):
+    returns (flips, energy taken from the walker, near-tie flags)."""
+    dE = np.ascontiguousarray(dE, dtype=np.float64)
+    flip = np.zeros(len(dE), dtype=np.int32)
+    tie = np.zeros(len(dE), dtype=np.int32)
+    D = lib().orc_micsa_walker(len(dE), _p(dE), float(beta), float(u), _p(flip), tie_eps, _p(tie))
+    return flip, D, tie
 
 
 def cc_labels(L, sa, sb):
@@ -249,10 +278,16 @@ class OracleSample:
             for r in range(self.n_res):
                 lat = g * self.nslot + int(self.perm[g * self.nslot + self.n_temps + r])
                 for sw in range(n_sweeps):
-                    _, ties, _ = sweep(self.L, self.J, self.spins[lat], self.beta[-1], self.seed, lat,
-                                       PRETHERM_EMCS, self.pretherm_done + sw, self.cfg.order,
-                                       self.cfg.rule, tie_eps=self.cfg.tie_eps)
-                    self.n_ties[0] += len(ties)
+                    if self.cfg.rule == RULE_MICSA:
+                        _, _, _, nt = sweep_micsa(self.L, self.J, self.spins[lat], self.beta[-1], self.seed,
+                                                  g * self.n_res + r, 1, PRETHERM_EMCS, self.pretherm_done + sw,
+                                                  tie_eps=self.cfg.tie_eps)
+                    else:
+                        _, ties, _ = sweep(self.L, self.J, self.spins[lat], self.beta[-1], self.seed, lat,
+                                           PRETHERM_EMCS, self.pretherm_done + sw, self.cfg.order,
+                                           self.cfg.rule, tie_eps=self.cfg.tie_eps)
+                        nt = len(ties)
+                    self.n_ties[0] += nt
                 self.E_lat[lat] = energy(self.L, self.J, self.spins[lat])
         self.pretherm_done += n_sweeps
 

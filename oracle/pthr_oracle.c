@@ -30,7 +30,9 @@
  *                        T_max.
  *   Sec. 5 (round trips) T_max -> T_min -> T_max excursions of a clone.
  *   App. A.1             Delta E = 2 s_i sum_j J_ij s_j, Metropolis
- *                        acceptance min{1, exp(-Delta E / T)}.
+ *                        acceptance min{1, exp(-Delta E / T)}; MicSA: a spin
+ *                        flips when its walker holds at least Delta E, which
+ *                        is then taken from the walker.
  * Readings where the paper is silent are stated at the point of use below.
  */
 #include <math.h>
@@ -69,7 +71,7 @@ void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t ou
 
 /* Stream tags (fourth counter word, low byte). */
 enum { TAG_INIT = 0, TAG_SWEEP = 1, TAG_ACU = 2, TAG_PT = 3, TAG_SINGLE = 4,
-       TAG_COUPLING = 5, TAG_SWEEP_LEX = 6 };
+       TAG_COUPLING = 5, TAG_SWEEP_LEX = 6, TAG_MICSA = 7 };
 
 /* One 32-bit Philox word: key = the sample seed, counter (c0, c1, c2, c3). */
 static uint32_t rng_word(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2,
@@ -176,7 +178,7 @@ void orc_init_spins(int L, uint64_t seed, int lat, int8_t *s)
 /* a2/a3: one full-lattice sweep at inverse temperature beta.               */
 /* ------------------------------------------------------------------------ */
 enum { ORDER_CHECKERBOARD = 0, ORDER_LEXICOGRAPHIC = 1 };
-enum { RULE_METROPOLIS = 0, RULE_HEATBATH = 1 };
+enum { RULE_METROPOLIS = 0, RULE_HEATBATH = 1, RULE_MICSA = 2 };
 
 /* The random word that the checkerboard sweep uses at site i.
  * Sites of colour c = (x+y+z)&1 in row r = y + L z sit at x = 2m + p; the
@@ -268,6 +270,108 @@ long orc_sweep(int L, const double *J, int8_t *s, double beta, uint64_t seed,
                 if (dE) *dE += 2.0 * s[i] * h;
                 s[i] = (int8_t)(-s[i]);
                 accepted++;
+            }
+        }
+    }
+    return accepted;
+}
+
+/* ------------------------------------------------------------------------ */
+/* a2 variant: microcanonical simulated annealing (MicSA; Sec. 3 item i,     */
+/* App. A.1: a walker holds an energy; a spin flips when the walker has at   */
+/* least Delta E, which is then taken from the walker).                      */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * One walker serving n sites in order.  Reading of the walker's initial
+ * energy and refresh (the paper defers them to its MicSA reference): the
+ * walker is drawn afresh from the canonical distribution of a non-negative
+ * energy at temperature T, E_w = -T ln u, each time it starts its sites, so
+ * that (spins, walker) keep the weight exp(-(H + E_w)/T).  Site k flips iff
+ * Delta E_k < E_w - D, D = sum of the Delta E already taken by earlier
+ * flips of this walker, i.e. iff X_k = D + Delta E_k <= 0 or
+ * u < exp(-beta X_k); a flip adds Delta E_k to D.  u is the walker's
+ * uniform.  tie[k] (if not NULL) is set for a near-tie decision:
+ * |u - exp(-beta X)| < tie_eps, 0 < |beta X| < tie_eps, or an offset X
+ * that FP32 cannot hold exactly (X = 0 is exact and flips on both sides).
+ * flip[k] receives 0/1; returns D.
+ */
+double orc_micsa_walker(int n, const double *dE, double beta, double u, int *flip,
+                        double tie_eps, int *tie)
+{
+    double D = 0.0;
+    for (int k = 0; k < n; k++) {
+        double X = D + dE[k];
+        int f;
+        int t = (X != 0.0 && fabs(beta * X) < tie_eps) || (double)(float)X != X;
+        if (X <= 0.0) {
+            f = 1;
+        } else {
+            double p = exp(-beta * X);
+            f = (u < p);
+            if (fabs(u - p) < tie_eps) t = 1;
+        }
+        if (tie) tie[k] = t;
+        flip[k] = f;
+        if (f) D += dE[k];
+    }
+    return D;
+}
+
+/*
+ * One MicSA sweep of lattice s in checkerboard order.  Sites of colour c in
+ * row r = y + L z sit at x = 2m + p; the walker of group (r, j) serves the
+ * sites m = 4j .. 4j+3 (those that exist) in ascending m, and a new walker
+ * starts at every group of every colour pass.  Its uniform is word e & 3 of
+ * the call (r W + j, (e >> 2) | kind << 24, emcs, TAG_MICSA | c << 8 |
+ * sweep << 9), where e is the lattice's position within its kind (PT
+ * clones: group * N_T + temperature index; reservoir: group * N_res + slot)
+ * and kind = 1 for reservoir clones.  Within a group the sites are not
+ * neighbours, so every Delta E of the group is taken before any of its
+ * flips.  Returns the number of flips; *dE accumulates the energy change;
+ * *n_tie_decisions counts near-tie decisions and tie_sites receives every
+ * site a near tie may have changed (*n_tie_sites of them).
+ */
+long orc_sweep_micsa(int L, const double *J, int8_t *s, double beta, uint64_t seed, int e, int kind,
+                     uint32_t emcs, uint32_t sweep, double tie_eps, int32_t *tie_sites, int max_ties,
+                     int *n_tie_sites, int *n_tie_decisions, double *dE_total)
+{
+    int W = (L / 2 + 3) / 4, Lh = L / 2;
+    long accepted = 0;
+    for (int c = 0; c < 2; c++) {
+        for (int r = 0; r < L * L; r++) {
+            int y = r % L, z = r / L, p = (c + y + z) & 1;
+            for (int j = 0; j < W; j++) {
+                int sites[4], n = 0;
+                double dE[4];
+                int flip[4], tie[4];
+                for (int k = 0; k < 4; k++) {
+                    int m = 4 * j + k;
+                    if (m >= Lh) break;
+                    int i = (2 * m + p) + L * r;
+                    sites[n] = i;
+                    dE[n] = 2.0 * s[i] * local_field(L, J, s, i);
+                    n++;
+                }
+                uint32_t w = rng_word(seed, (uint32_t)(r * W + j), ((uint32_t)e >> 2) | ((uint32_t)kind << 24),
+                                      emcs, TAG_MICSA | ((uint32_t)c << 8) | (sweep << 9), e & 3);
+                orc_micsa_walker(n, dE, beta, uniform24(w), flip, tie_eps, tie);
+                /* a near tie at site k may change k and, through the walker,
+                 * every later site of the group: all of them are logged */
+                int tied = 0;
+                for (int k = 0; k < n; k++) {
+                    if (tie[k] && n_tie_decisions) (*n_tie_decisions)++;
+                    tied |= tie[k];
+                    if (tied && n_tie_sites) {
+                        if (*n_tie_sites < max_ties && tie_sites) tie_sites[*n_tie_sites] = sites[k];
+                        (*n_tie_sites)++;
+                    }
+                    if (flip[k]) {
+                        if (dE_total) *dE_total += dE[k];
+                        s[sites[k]] = (int8_t)(-s[sites[k]]);
+                        accepted++;
+                    }
+                }
             }
         }
     }
@@ -626,11 +730,17 @@ void orc_emcs(const orc_cfg *cfg, const double *J, const double *T, const double
             int lat = g * nslot + st->perm[g * nslot + pos];
             double b = in_res ? beta_max : beta[pos];
             int nsw = in_res ? cfg->res_sweeps_per_emcs : cfg->sweeps_per_emcs;
+            int e = in_res ? g * cfg->n_res + (pos - cfg->n_temps) : g * cfg->n_temps + pos;
             for (int sw = 0; sw < nsw; sw++) {
                 double dE = 0.0;
-                st->flips[lat] += orc_sweep(L, J, st->spins + (size_t)lat * V, b, seed, lat,
-                                            emcs, (uint32_t)sw, cfg->order, cfg->rule,
-                                            cfg->tie_eps, 0, NULL, 0, &ties_local, &dE);
+                if (cfg->rule == RULE_MICSA)
+                    st->flips[lat] += orc_sweep_micsa(L, J, st->spins + (size_t)lat * V, b, seed, e, in_res,
+                                                      emcs, (uint32_t)sw, cfg->tie_eps, NULL, 0, NULL,
+                                                      &ties_local, &dE);
+                else
+                    st->flips[lat] += orc_sweep(L, J, st->spins + (size_t)lat * V, b, seed, lat,
+                                                emcs, (uint32_t)sw, cfg->order, cfg->rule,
+                                                cfg->tie_eps, 0, NULL, 0, &ties_local, &dE);
             }
         }
     }

@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libpthr.so")
  PTHR_E_BOUNDS) = range(8)
 STATUS_NAMES = {0: "PTHR_OK", 1: "PTHR_E_INVAL", 2: "PTHR_E_NOMEM", 3: "PTHR_E_CUDA",
                 4: "PTHR_E_NOCONVERGE", 5: "PTHR_E_TIMEOUT", 6: "PTHR_E_STATE", 7: "PTHR_E_BOUNDS"}
-METROPOLIS, HEATBATH = 0, 1
+METROPOLIS, HEATBATH, MICSA = 0, 1, 2
 CLUSTER_OFF, CLUSTER_ACU, CLUSTER_SINGLE = 0, 1, 2
 SWAP_PT, SWAP_ER = 1, 2
 OBS_MEASURE, OBS_READ_HOST, OBS_READ_DEVICE, OBS_RESET, OBS_CHAOS = 1, 2, 4, 8, 16

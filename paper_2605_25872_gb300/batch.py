@@ -15,7 +15,7 @@ import torch
 from . import _lib
 from ._lib import check
 
-RULES = {"metropolis": _lib.METROPOLIS, "heatbath": _lib.HEATBATH}
+RULES = {"metropolis": _lib.METROPOLIS, "heatbath": _lib.HEATBATH, "micsa": _lib.MICSA}
 LIVE = weakref.WeakSet()      # open batches (the tests check their guard blocks)
 CLUSTERS = {"off": _lib.CLUSTER_OFF, "acu": _lib.CLUSTER_ACU, "single": _lib.CLUSTER_SINGLE}
 

@@ -84,7 +84,7 @@ pthr_status check_config(const pthr_config *c) {
         c->res_sweeps_per_emcs >= (1 << 22))
         return fail(nullptr, PTHR_E_INVAL, "sweeps per EMCS must be in [0, 2^22)");
     if (c->acu_interval < 1) return fail(nullptr, PTHR_E_INVAL, "acu_interval must be >= 1");
-    if (c->update_rule != PTHR_METROPOLIS && c->update_rule != PTHR_HEATBATH)
+    if (c->update_rule != PTHR_METROPOLIS && c->update_rule != PTHR_HEATBATH && c->update_rule != PTHR_MICSA)
         return fail(nullptr, PTHR_E_INVAL, "unknown update_rule %d", c->update_rule);
     if (c->cluster_mode < PTHR_CLUSTER_OFF || c->cluster_mode > PTHR_CLUSTER_SINGLE)
         return fail(nullptr, PTHR_E_INVAL, "unknown cluster_mode %d", c->cluster_mode);

@@ -21,7 +21,8 @@ constexpr int SMEM_WORDS = 4096;          // uint4 words: 64 KB of shared memory
 // Shared-memory loads: each thread reads 16 bytes per load; a warp's 32
 // loads cover 512 consecutive bytes (four wavefronts, no bank conflict).
 // The eight addresses of a loop trip are fixed, so no index arithmetic
-// competes with the loads.
+// competes with the loads; the loads are volatile, so the compiler cannot
+// hoist them out of the loop.
 __global__ void __launch_bounds__(PEAK_THREADS) peak_smem_kernel(uint32_t *sink, int iters) {
     extern __shared__ __align__(16) uint4 buf[];
     const int tid = threadIdx.x;
@@ -33,7 +34,7 @@ __global__ void __launch_bounds__(PEAK_THREADS) peak_smem_kernel(uint32_t *sink,
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
             uint32_t x, y, z, w;
-            asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+            asm volatile("ld.volatile.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
                          : "=r"(x), "=r"(y), "=r"(z), "=r"(w) : "r"(base + 16u * 512u * (uint32_t)u));
             a0 ^= x ^ y;
             a1 ^= z ^ w;
@@ -46,10 +47,12 @@ __global__ void __launch_bounds__(PEAK_THREADS) peak_smem_kernel(uint32_t *sink,
 // L2 loads that bypass L1 (.cg): 16 bytes per thread and load, grid-stride
 // over a buffer small enough to stay resident in L2 (n16 a multiple of the
 // grid's thread count, so every thread loads the same number of words).
+// The pass loop is not unrolled, so each pass issues its loads again.
 __global__ void __launch_bounds__(PEAK_THREADS) peak_l2_kernel(const uint4 *buf, size_t n16, uint32_t *sink,
                                                               int passes) {
     const size_t stride = (size_t)gridDim.x * blockDim.x;
     uint32_t a0 = 0, a1 = 0;
+#pragma unroll 1
     for (int p = 0; p < passes; ++p) {
 #pragma unroll 4
         for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n16; i += stride) {

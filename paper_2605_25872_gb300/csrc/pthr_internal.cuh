@@ -12,6 +12,8 @@
 //   init spins  (i>>2, lattice, 0, TAG_INIT)              word i & 3
 //   sweep       (r*W + (m>>2), lattice, emcs, TAG_SWEEP | c<<8 | sweep<<9)
 //                                                        word m & 3
+//   MicSA walker (r*W + j, (e>>2) | kind<<24, emcs, TAG_MICSA | c<<8 | sweep<<9)
+//                                   word e & 3, e = position within the kind
 //   ACU sign    (label, pair*n_temps + k, emcs, TAG_ACU)  word 0, top bit
 //   PT          (k, 2*group + phase, emcs, TAG_PT)        word 0
 //   single seed (0, pair*n_temps + k, emcs, TAG_SINGLE)   word 0
@@ -27,7 +29,7 @@
 namespace pthr {
 
 constexpr uint32_t TAG_INIT = 0, TAG_SWEEP = 1, TAG_ACU = 2, TAG_PT = 3, TAG_SINGLE = 4,
-                   TAG_COUPLING = 5;
+                   TAG_COUPLING = 5, TAG_MICSA = 7;
 constexpr uint32_t PRETHERM_EMCS = 0xFFFFFFFFu;
 constexpr uint32_t STATUS_NOCONVERGE = 1u;
 constexpr uint32_t STATUS_BOUNDS = 2u;

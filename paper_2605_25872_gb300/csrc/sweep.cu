@@ -23,6 +23,7 @@ int sweep_kt_options(int L, int rule, int *out) {
     int n = 0;
 #define X(LL, KK) if (L == LL) out[n++] = KK;
     if (rule == PTHR_HEATBATH) { PTHR_SWEEP_HB_TABLE(X) }
+    else if (rule == PTHR_MICSA) { PTHR_SWEEP_MICSA_TABLE(X) }
     else { PTHR_SWEEP_METRO_A_TABLE(X) PTHR_SWEEP_METRO_B_TABLE(X) }
 #undef X
     return n;
@@ -34,6 +35,8 @@ cudaError_t launch_sweep(const SweepArgs &a, int blocks, int threads, int KT, cu
     cudaError_t e = cudaErrorInvalidValue;
     if (a.b.rule == PTHR_HEATBATH) {
         if (launch_sweep_hb(a, blocks, threads, KT, smem, st, &e)) return e;
+    } else if (a.b.rule == PTHR_MICSA) {
+        if (launch_sweep_micsa(a, blocks, threads, KT, smem, st, &e)) return e;
     } else {
         if (launch_sweep_metro_a(a, blocks, threads, KT, smem, st, &e)) return e;
         if (launch_sweep_metro_b(a, blocks, threads, KT, smem, st, &e)) return e;

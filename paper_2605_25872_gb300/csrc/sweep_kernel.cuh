@@ -18,7 +18,9 @@
 // word), Delta E = 2 t_i and the move is accepted iff u < 2^(tb t_i) with
 // tb = -2 log2(e) / T, i.e. iff the FP32 difference u - p is negative; the
 // four sign bits of one group become the byte flip mask with three byte
-// permutes.  Heat bath: s_i = +1 iff u < 1 / (1 + 2^(tb h_i)).
+// permutes.  Heat bath: s_i = +1 iff u < 1 / (1 + 2^(tb h_i)).  MicSA
+// (App. A.1): a walker per (lattice, 4-site group, colour pass) starts with
+// energy -T ln u and pays for the group's flips in order.
 #pragma once
 
 #include "kernels.cuh"
@@ -313,8 +315,12 @@ sweep_kernel(SweepArgs a) {
         s_lat[tid] = g * b.NSLOT + clone;
         // round 1 of every sweep draw of this lattice starts from M0 times
         // its round-0 word 0, which depends on the lattice and the block only
+        // (MicSA: the walker draws are keyed by the position e within the
+        // kind, four positions per Philox call, instead of by the lattice)
+        const uint32_t c1 = RULE == PTHR_MICSA ? ((uint32_t)(e >> 2) | ((uint32_t)kind << 24))
+                                                : (uint32_t)(g * b.NSLOT + clone);
         uint32_t ph, pl;
-        mul_wide(0xD2511F53u, rng_x1 ^ (uint32_t)(g * b.NSLOT + clone), ph, pl);
+        mul_wide(0xD2511F53u, rng_x1 ^ c1, ph, pl);
         // -2 beta log2(e): exp(-beta dE) = 2^(tb t) with dE = 2 t
         s_lr[tid] = make_uint4(ph, pl, __float_as_uint(b.tabTb[kind ? b.NT - 1 : pos]), 0u);
         s_flips[tid] = 0u;
@@ -442,7 +448,7 @@ sweep_kernel(SweepArgs a) {
         qc1 = group_geo<L>(g0, 1);
     }
     for (int sw = 0; sw < nsw; ++sw) {
-        const uint32_t c3base = TAG_SWEEP | ((uint32_t)(sweep_base + sw) << 9);
+        const uint32_t c3base = (RULE == PTHR_MICSA ? TAG_MICSA : TAG_SWEEP) | ((uint32_t)(sweep_base + sw) << 9);
         for (int c = 0; c < 2; ++c) {
             const uint32_t c3 = c3base | ((uint32_t)c << 8);
             for (int gi = 0; gi < GP; ++gi) {
@@ -531,6 +537,7 @@ sweep_kernel(SweepArgs a) {
                     const int nv = Lh - 4 * j;
                     vmask = nv >= 4 ? 0x80808080u : (0x80808080u >> (8 * (4 - nv)));
                 }
+                u4 walker_rnd{};       // MicSA: one Philox call serves four positions
 #pragma unroll
                 for (int jj = 0; jj < KT; ++jj) {
                     const int k = kbase + jj;
@@ -541,11 +548,53 @@ sweep_kernel(SweepArgs a) {
                     const uint32_t xs = __byte_perm(S[q.wA], S[q.wB], q.selx);
                     const uint32_t wyp = S[q.yp], wym = S[q.ym], wzp = S[q.zp], wzm = S[q.zm];
                     const uint4 lr = s_lr[k];
-                    const u4 rnd = philox10_sweep(lr.x, lr.y, rng, rk0, rk1);
+                    u4 rnd;
+                    if (RULE == PTHR_MICSA) {
+                        if (jj == 0 || ((e0 + k) & 3) == 0)
+                            walker_rnd = philox10_sweep(lr.x, lr.y, rng, rk0, rk1);
+                        rnd = walker_rnd;
+                    } else {
+                        rnd = philox10_sweep(lr.x, lr.y, rng, rk0, rk1);
+                    }
                     const uint32_t rw[4] = {rnd.x, rnd.y, rnd.z, rnd.w};
                     const float tb = __uint_as_float(lr.z);
                     uint32_t fm;
-                    if (RULE == PTHR_METROPOLIS) {
+                    if (RULE == PTHR_MICSA) {
+                        // one walker per (lattice, group, colour pass) with
+                        // energy -T ln u; site kk flips iff u < 2^(tb y), y =
+                        // D + t_kk, D the share already taken by this pass's
+                        // flips (in units of t = Delta E / 2), then D = y
+                        const uint32_t X = 0x3F3F3F3Fu;
+                        const uint32_t pxa = own ^ xa ^ X, pxs = own ^ xs ^ X;
+                        const uint32_t pyp = own ^ wyp ^ X, pym = own ^ wym ^ X;
+                        const uint32_t pzp = own ^ wzp ^ X, pzm = own ^ wzm ^ X;
+                        float tv[4];
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) {
+                            f2 tt = mul2(Jp[h][0], spin_pair(pxa, h));
+                            tt = fma2(Jp[h][1], spin_pair(pxs, h), tt);
+                            tt = fma2(Jp[h][2], spin_pair(pyp, h), tt);
+                            tt = fma2(Jp[h][3], spin_pair(pym, h), tt);
+                            tt = fma2(Jp[h][4], spin_pair(pzp, h), tt);
+                            tt = fma2(Jp[h][5], spin_pair(pzm, h), tt);
+                            unpack2(tt, tv[2 * h], tv[2 * h + 1]);
+                        }
+                        const int sel = (e0 + k) & 3;
+                        const uint32_t wsel = sel == 0 ? rw[0] : (sel == 1 ? rw[1] : (sel == 2 ? rw[2] : rw[3]));
+                        const float uw = uniform24f(wsel);
+                        float D = 0.f;
+                        fm = 0u;
+#pragma unroll
+                        for (int kk = 0; kk < 4; ++kk) {
+                            const float y = D + tv[kk];
+                            const bool flip = uw < fast_exp2(tb * y);
+                            if (flip) {
+                                D = y;
+                                fm |= 0x80u << (8 * kk);
+                            }
+                        }
+                        fm &= vmask;
+                    } else if (RULE == PTHR_METROPOLIS) {
                         // bytes 0x3F where s_i s_j = +1, 0xBF where -1
                         const uint32_t X = 0x3F3F3F3Fu;
                         const uint32_t pxa = own ^ xa ^ X, pxs = own ^ xs ^ X;

@@ -18,6 +18,9 @@
 #define PTHR_SWEEP_HB_TABLE(X) \
     X(2, 1) X(4, 2) X(6, 8) X(8, 8) X(10, 32) X(12, 32) X(14, 32) X(16, 32) X(18, 16) X(20, 8) \
     X(22, 4) X(24, 4)
+#define PTHR_SWEEP_MICSA_TABLE(X) \
+    X(2, 1) X(4, 2) X(6, 8) X(8, 8) X(10, 16) X(12, 16) X(14, 16) X(16, 16) X(18, 16) X(20, 8) \
+    X(22, 4) X(24, 4)
 
 namespace pthr {
 struct SweepArgs;
@@ -27,4 +30,6 @@ bool launch_sweep_metro_b(const SweepArgs &a, int blocks, int threads, int KT, s
                           cudaStream_t st, cudaError_t *err);
 bool launch_sweep_hb(const SweepArgs &a, int blocks, int threads, int KT, size_t smem,
                      cudaStream_t st, cudaError_t *err);
+bool launch_sweep_micsa(const SweepArgs &a, int blocks, int threads, int KT, size_t smem,
+                        cudaStream_t st, cudaError_t *err);
 }  // namespace pthr

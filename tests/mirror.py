@@ -14,7 +14,7 @@ import numpy as np
 
 import oracle as O
 
-RULE = {"metropolis": O.RULE_METROPOLIS, "heatbath": O.RULE_HEATBATH}
+RULE = {"metropolis": O.RULE_METROPOLIS, "heatbath": O.RULE_HEATBATH, "micsa": O.RULE_MICSA}
 CLUSTER = {"off": O.CLUSTER_OFF, "acu": O.CLUSTER_ACU, "single": O.CLUSTER_SINGLE}
 
 
@@ -67,14 +67,21 @@ class Mirror:
                     lat = smp.lattice_at(g, pos)
                     b = self.beta[-1] if in_res else self.beta[pos]
                     base = smp.pretherm_done if pretherm else (self.res_off if in_res else self.pt_off)
+                    e = g * c.n_res + (pos - c.n_temps) if in_res else g * c.n_temps + pos
                     for sw in range(nsw):
-                        acc, tl, dE = O.sweep(self.L, smp.J, smp.spins[lat], b, smp.seed, lat,
-                                              emcs & 0xFFFFFFFF, base + sw, rule=self.rule,
-                                              tie_eps=self.tie_eps,
-                                              field_err_bound=self.field_err_bound)
+                        if self.rule == O.RULE_MICSA:
+                            acc, tl, dE, nt = O.sweep_micsa(self.L, smp.J, smp.spins[lat], b, smp.seed, e,
+                                                            int(in_res), emcs & 0xFFFFFFFF, base + sw,
+                                                            tie_eps=self.tie_eps)
+                        else:
+                            acc, tl, dE = O.sweep(self.L, smp.J, smp.spins[lat], b, smp.seed, lat,
+                                                  emcs & 0xFFFFFFFF, base + sw, rule=self.rule,
+                                                  tie_eps=self.tie_eps,
+                                                  field_err_bound=self.field_err_bound)
+                            nt = len(tl)
                         smp.flips[lat] += acc
                         self.decisions += self.V
-                        self.n_ties += len(tl)
+                        self.n_ties += nt
                         if len(tl):
                             ties.setdefault((s, lat), set()).update(int(t) for t in tl)
                     smp.E_lat[lat] = O.energy(self.L, smp.J, smp.spins[lat])

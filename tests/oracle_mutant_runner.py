@@ -18,6 +18,8 @@ PINS = [
     T.test_pair_moments_enumeration_agrees_with_the_enumerator,
     T.test_sweep_incremental_energy_equals_recomputed,
     T.test_sweep_is_gauge_covariant,
+    T.test_micsa_walker_leaves_the_boltzmann_weight_stationary,
+    T.test_micsa_sweep_incremental_energy_equals_recomputed,
     lambda: T.test_cc_labels_match_scipy(4),
     T.test_acu_invariants,
     T.test_er_fifo_and_round_trips,

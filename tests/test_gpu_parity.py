@@ -167,6 +167,20 @@ def test_sweep_trajectory_parity(L, rule):
         np.testing.assert_array_equal(gpu.flips.cpu().numpy(), np.stack([s.flips for s in mir.samples]))
 
 
+@pytest.mark.parametrize("L", [2, 4, 6, 8, 12, 16, 18])
+def test_micsa_sweep_trajectory_parity(L):
+    """MicSA (App. A.1): walkers per (clone, group, colour pass) keyed by the
+    clone's position; bit-exact against the oracle up to counted near ties."""
+    cfg = BatchConfig(L=L, n_samples=2, n_temps=6, n_replicas=2, n_res=2, rule="micsa",
+                      t_min=0.2, t_max=1.6)
+    gpu, mir = make(cfg, seed=400 + L)
+    n = 100 if L < 12 else (40 if L <= 16 else 10)
+    diverged, decisions = check_sweep_parity(gpu, mir, n)
+    assert diverged <= max(1, TIE_RATE_MAX * decisions)
+    if diverged == 0:
+        np.testing.assert_array_equal(gpu.flips.cpu().numpy(), np.stack([s.flips for s in mir.samples]))
+
+
 def test_sweep_parity_1000_sweeps_plain_config():
     """Config 1 shape (L=4, 12 temperatures, 4 replicas + 4 reservoir clones):
     10^3 sweeps of every clone, bit-exact up to counted near ties."""
@@ -352,7 +366,8 @@ def test_full_emcs_parity_plain_config():
 
 
 @pytest.mark.parametrize("cluster,rule,er", [("acu", "metropolis", True), ("single", "metropolis", True),
-                                             ("acu", "heatbath", False), ("off", "metropolis", False)])
+                                             ("acu", "heatbath", False), ("off", "metropolis", False),
+                                             ("acu", "micsa", True)])
 def test_full_emcs_parity_batched(cluster, rule, er):
     cfg = BatchConfig(L=8, n_samples=4, n_temps=8, n_replicas=4, n_res=2 if er else 0,
                       sweeps_per_emcs=2, res_sweeps_per_emcs=6, er_on=er, cluster=cluster, rule=rule)
@@ -403,6 +418,14 @@ def test_tuning_does_not_change_results():
               {"pt_lattices_per_block": 7, "sweep_threads": 64, "cluster_threads": 128},
               {"pt_lattices_per_block": 32, "res_lattices_per_block": 16, "sweep_threads": 256}):
         b = Batch(cfg, couplings=J, seeds=seeds, tuning=t)
+        b.emcs(5)
+        _same(_state(ref), _state(b))
+    # MicSA draws one Philox call per four positions: also independent of the shape
+    cm = BatchConfig(**{**cfg.__dict__, "rule": "micsa"})
+    ref = Batch(cm, couplings=J, seeds=seeds)
+    ref.emcs(5)
+    for t in ({"pt_lattices_per_block": 3, "res_lattices_per_block": 5}, {"pt_lattices_per_block": 13}):
+        b = Batch(cm, couplings=J, seeds=seeds, tuning=t)
         b.emcs(5)
         _same(_state(ref), _state(b))
 

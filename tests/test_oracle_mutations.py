@@ -43,6 +43,9 @@ MUTANTS = [
     ("overlap accumulated as |q|", "o[3] += r[0];", "o[3] += fabs(r[0]);"),
     ("temperature grid divided by N_T", "(t_max - t_min) / (double)(n_temps - 1);",
      "(t_max - t_min) / (double)(n_temps);"),
+    ("MicSA walker not debited", "        if (f) D += dE[k];\n", ""),
+    ("MicSA walker credited instead of debited", "if (f) D += dE[k];", "if (f) D -= dE[k];"),
+    ("MicSA energy change of a flip dropped", "if (dE_total) *dE_total += dE[k];", "if (dE_total) *dE_total += 0.0;"),
 ]
 
 

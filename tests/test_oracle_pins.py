@@ -102,6 +102,88 @@ def test_sweep_incremental_energy_equals_recomputed():
         assert E0 + tot == O.energy(L, J, s)
 
 
+def test_micsa_sweep_incremental_energy_equals_recomputed():
+    """MicSA (App. A.1): the energy the walkers hand to the lattice, summed
+    over accepted flips, equals the change of the recomputed energy."""
+    for L in (4, 6, 8):
+        J = _rand_J(L, 5 * L)
+        s = W.random_spins(L ** 3, 9 * L)
+        E0 = O.energy(L, J, s)
+        tot = 0.0
+        for sw in range(20):
+            _, _, dE, _ = O.sweep_micsa(L, J, s, 1.0 / 0.5, 321, 3, 0, 7, sw)
+            tot += dE
+        assert E0 + tot == O.energy(L, J, s)
+
+
+def _walker_kernel(h, beta):
+    """Exact transition matrix of one MicSA walker over n non-interacting
+    spins with fields h (the sites of one checkerboard group): the walker's
+    uniform u is integrated out exactly, the outcome being constant between
+    the breakpoints exp(-beta X) of every offset X the walker can reach."""
+    n = len(h)
+    states = [np.array([1 - 2 * ((st >> k) & 1) for k in range(n)]) for st in range(2 ** n)]
+    K = np.zeros((2 ** n, 2 ** n))
+    for a, s in enumerate(states):
+        dE = 2.0 * s * h
+        X = {0.0}
+        for k in range(n):
+            X = X | {x + dE[k] for x in X}
+        cuts = sorted({0.0, 1.0} | {float(np.exp(-beta * x)) for x in X if x > 0})
+        for lo, hi in zip(cuts[:-1], cuts[1:]):
+            if hi <= lo:
+                continue
+            u = 0.5 * (lo + hi)
+            flip, D, _ = O.micsa_walker(dE, beta, u)
+            assert D <= -np.log(u) / beta + 1e-12          # the walker never goes negative
+            t = s * np.where(flip == 1, -1, 1)
+            b = sum(((1 - t[k]) // 2) << k for k in range(n))
+            K[a, b] += hi - lo
+    return states, K
+
+
+def test_micsa_walker_leaves_the_boltzmann_weight_stationary():
+    """Detailed balance of the MicSA move (App. A.1) on its own: a walker
+    drawn from the canonical exponential at T and debited by every accepted
+    Delta E maps the Boltzmann weight of its n independent sites onto itself
+    (exactly, with the walker's uniform integrated out)."""
+    rng = np.random.default_rng(99)
+    for n in (1, 2, 3, 4):
+        for rep in range(6):
+            h = rng.standard_normal(n) * 2.0
+            beta = float(rng.uniform(0.5, 4.0))
+            states, K = _walker_kernel(h, beta)
+            np.testing.assert_allclose(K.sum(1), 1.0, atol=1e-12)
+            pi = np.array([np.exp(beta * float(np.dot(s, h))) for s in states])
+            pi /= pi.sum()
+            np.testing.assert_allclose(pi @ K, pi, atol=1e-12)
+
+
+def test_micsa_chain_agrees_with_metropolis_at_L4():
+    """At L = 4 a MicSA walker serves two sites, so the 2x2x2 enumeration no
+    longer reaches it: the full MicSA PTHR chain is compared with the
+    Metropolis chain (pinned against enumeration) on the same sample: <e>
+    and <q^2> agree within 5 combined standard errors at every T."""
+    L, nT = 4, 4
+    J = _rand_J(L, 77)
+    est = {}
+    for rule in (O.RULE_METROPOLIS, O.RULE_MICSA):
+        smp = O.OracleSample(L, nT, 0.5, 1.6, seed=11, J=J, n_groups=4, n_res=2, sweeps_per_emcs=1,
+                             res_sweeps_per_emcs=4, rule=rule)
+        smp.emcs(300)
+        blocks = []
+        for b in range(16):
+            before = smp.obs.copy()
+            smp.emcs(400)
+            d = smp.obs - before
+            blocks.append(np.stack([d[:, 1] / (d[:, 0] * 4), d[:, 4] / (d[:, 0] * 2)], 1))
+        blocks = np.array(blocks)
+        est[rule] = (blocks.mean(0), blocks.std(0, ddof=1) / np.sqrt(len(blocks)))
+    (m1, e1), (m2, e2) = est[O.RULE_METROPOLIS], est[O.RULE_MICSA]
+    z = np.abs(m1 - m2) / np.sqrt(e1 ** 2 + e2 ** 2)
+    assert np.all(z < 5.0), z
+
+
 def test_sweep_is_gauge_covariant():
     """A Metropolis sweep with couplings tau J tau started from tau s, driven
     by the same random numbers, ends in tau times the original end state.  A
@@ -479,6 +561,7 @@ def _chain_vs_exact(rule, order, cluster, er_on, n_blocks=20, block=800, seed=5)
     (O.RULE_HEATBATH, O.ORDER_CHECKERBOARD, O.CLUSTER_ACU, True),
     (O.RULE_METROPOLIS, O.ORDER_LEXICOGRAPHIC, O.CLUSTER_OFF, False),
     (O.RULE_METROPOLIS, O.ORDER_CHECKERBOARD, O.CLUSTER_SINGLE, True),
+    (O.RULE_MICSA, O.ORDER_CHECKERBOARD, O.CLUSTER_ACU, True),
 ])
 def test_pthr_chain_reproduces_exact_averages_on_2x2x2(rule, order, cluster, er_on):
     """The full EMCS (sweeps, cluster move, PT, ER) samples the Boltzmann

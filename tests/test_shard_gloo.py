@@ -65,3 +65,58 @@ def test_gather_and_reduce_over_two_gloo_ranks(tmp_path, n_total):
     for r in range(world):
         np.testing.assert_array_equal(np.load(tmp_path / f"g{r}.npy"), full)
         np.testing.assert_allclose(np.load(tmp_path / f"s{r}.npy"), full.sum(axis=0), rtol=1e-12)
+
+
+def _pthr_worker(rank, world, port, n_total, n_emcs, out_dir):
+    """Each rank runs the FP64 oracle on its own shard of the samples (seeds
+    and couplings from the global sample id) and the per-sample accumulators
+    are gathered and the per-temperature sums reduced at the end."""
+    import torch.distributed as dist
+    import oracle as O
+    import workloads as W
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    first, count = sample_range(rank, world, n_total)
+    seeds = shard_seeds(W.SEED_BASE + 77, rank, world, n_total)
+    J = W.gaussian_couplings(4, n_total, 77)[first:first + count]
+    obs = []
+    for s in range(count):
+        smp = O.OracleSample(4, 6, 0.2, 1.6, int(seeds[s]), J=J[s].astype(np.float64), n_groups=4,
+                             n_res=2, sweeps_per_emcs=1, res_sweeps_per_emcs=4)
+        smp.prethermalize_reservoir(8)
+        smp.emcs(n_emcs)
+        obs.append(np.concatenate([smp.obs.ravel(), smp.round_trips.astype(np.float64)]))
+    local = np.array(obs).reshape(count, -1) if count else np.zeros((0, 6 * 8 + 4))
+    g = gather_samples(local)
+    tot = reduce_sums(local.sum(axis=0))
+    np.save(os.path.join(out_dir, f"pthr_g{rank}_{world}.npy"), g)
+    np.save(os.path.join(out_dir, f"pthr_s{rank}_{world}.npy"), tot)
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_sharded_oracle_pthr_equals_one_rank(tmp_path):
+    """Sample sharding (independent disorder samples): PTHR run on two gloo
+    ranks, each with its own contiguous shard, gives per-sample accumulators
+    and reduced sums identical to the same run on one rank -- the result does
+    not depend on the rank count (per-sample values bit for bit; the reduced
+    sums up to the order of the floating-point additions)."""
+    n_total, n_emcs = 5, 6
+    ctx = mp.get_context("spawn")
+    for world in (1, 2):
+        port = _free_port()
+        procs = [ctx.Process(target=_pthr_worker, args=(r, world, port, n_total, n_emcs, str(tmp_path)))
+                 for r in range(world)]
+        for p in procs:
+            p.start()
+        for p in procs:
+            p.join(timeout=300)
+            assert p.exitcode == 0
+    one = np.load(tmp_path / "pthr_g0_1.npy")
+    assert one.shape[0] == n_total
+    for r in range(2):
+        np.testing.assert_array_equal(np.load(tmp_path / f"pthr_g{r}_2.npy"), one)
+        # the reduction adds the same per-sample values in another order
+        np.testing.assert_allclose(np.load(tmp_path / f"pthr_s{r}_2.npy"), np.load(tmp_path / "pthr_s0_1.npy"),
+                                   rtol=1e-13, atol=1e-12)
