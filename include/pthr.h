@@ -315,6 +315,29 @@ PTHR_API pthr_status pthr_reservoir_autocorrelation(pthr_batch *b, int first, in
                                                     int sweeps_per_point, void *snapshot_device,
                                                     size_t snapshot_bytes, int64_t *out_device);
 
+/* The same measurement as pthr_reservoir_autocorrelation, for callers that
+ * cannot allocate device memory: a plugin inside a host program that owns
+ * every device allocation through its own pool, a control loop that must
+ * not wait on (or risk a failure of) the allocator part-way through a run,
+ * or a language binding with no way to obtain device memory.  The paper has
+ * no counterpart; this is an interface convenience only.
+ * Instead of a caller-provided snapshot it uses a fixed 8 MiB device array
+ * inside the library, which every GPU that loads the library keeps until
+ * the process exits; it allocates nothing (no cudaMalloc or cudaFree, no
+ * allocating library call).  The snapshot must fit in it: count *
+ * n_replicas * n_res * pthr_lattice_bytes(L) <= 8 MiB (128 samples of the
+ * L = 16, 4 x 4 reservoir), else PTHR_E_NOMEM and nothing runs; split
+ * larger batches into sample ranges.  The first call on a device looks up
+ * the array's address on that device (the batch's device must be current,
+ * else PTHR_E_INVAL); make that first call before any stream capture.
+ * Every call reuses the same array: each call writes every snapshot word it
+ * later reads, so nothing needs clearing between calls, but calls that
+ * overlap on the GPU (other streams, other batches, other threads) race on
+ * it and must be serialised by the caller.  Arguments, results and
+ * asynchrony are those of pthr_reservoir_autocorrelation. */
+PTHR_API pthr_status pthr_reservoir_autocorrelation_noalloc(pthr_batch *b, int first, int count, int n_points,
+                                                            int sweeps_per_point, int64_t *out_device);
+
 /* Guard check: every workspace sub-buffer is followed by a 256-byte guard
  * block written with a fixed pattern at creation (included in
  * pthr_required_bytes).  Synchronises the stream and compares every guard

@@ -33,7 +33,8 @@ EXPORTS = ("pthr_required_bytes", "pthr_buffer_info", "pthr_lattice_bytes", "pth
            "pthr_prethermalize_reservoir", "pthr_poll", "pthr_export_spins", "pthr_import_spins",
            "pthr_reset_samples", "pthr_set_active", "pthr_save", "pthr_load", "pthr_last_error",
            "pthr_version", "pthr_group_create", "pthr_group_emcs", "pthr_group_destroy",
-           "pthr_measure_peak", "pthr_check_canaries", "pthr_reservoir_autocorrelation")
+           "pthr_measure_peak", "pthr_check_canaries", "pthr_reservoir_autocorrelation",
+           "pthr_reservoir_autocorrelation_noalloc")
 PEAK_SMEM_READ, PEAK_L2_READ, PEAK_ALU, PEAK_FMA, PEAK_FMA2, PEAK_FP64 = range(6)
 
 
@@ -103,6 +104,7 @@ def load(path: str | None = None):
         "pthr_measure_peak": [i, vp, sz, vp, P(ctypes.c_double), P(ctypes.c_double)],
         "pthr_check_canaries": [vp, P(ctypes.c_int)],
         "pthr_reservoir_autocorrelation": [vp, i, i, i, i, vp, sz, vp],
+        "pthr_reservoir_autocorrelation_noalloc": [vp, i, i, i, i, vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)

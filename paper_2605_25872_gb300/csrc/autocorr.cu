@@ -9,9 +9,19 @@
 // over the clone's sites of s_i(t) s_i(t + tau) in integers (V minus twice
 // the sites that differ), summed over the sample's reservoir clones.  The
 // sweeps in between are ordinary reservoir pre-thermalisation sweeps.
+#include <mutex>
+
 #include "kernels.cuh"
 
 namespace pthr {
+
+// Snapshot storage for pthr_reservoir_autocorrelation_noalloc: a fixed
+// device array that every GPU which loads the library holds until the
+// process exits.  Host code must not use the name as an address (it is a
+// host-side stand-in); noalloc_snapshot() looks the device address up.
+constexpr size_t NOALLOC_SNAPSHOT_BYTES = size_t(8) << 20;
+static __device__ __align__(256) uint32_t g_noalloc_snapshot[NOALLOC_SNAPSHOT_BYTES / 4];
+
 namespace {
 
 // one block per (sample, reservoir clone): the clone's packed words
@@ -63,6 +73,28 @@ __global__ void overlap_kernel(Batch b, int first, int count, const uint32_t *sn
 }
 
 }  // namespace
+
+// Device address of g_noalloc_snapshot on the current device: looked up with
+// cudaGetSymbolAddress the first time a device asks (with that device
+// current), then cached per device.
+cudaError_t noalloc_snapshot(void **ptr, size_t *bytes) {
+    static std::mutex mu;
+    static void *addr[256] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 256) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!addr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_snapshot);
+        if (e != cudaSuccess) return e;
+        addr[dev] = p;
+    }
+    *ptr = addr[dev];
+    *bytes = NOALLOC_SNAPSHOT_BYTES;
+    return cudaSuccess;
+}
 
 cudaError_t launch_snapshot_reservoir(const Batch &b, int first, int count, uint32_t *snap, cudaStream_t st) {
     const int blocks = count * b.NR * b.NRES;

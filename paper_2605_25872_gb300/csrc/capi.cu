@@ -780,6 +780,30 @@ PTHR_API pthr_status pthr_reservoir_autocorrelation(pthr_batch *b, int first, in
     return PTHR_OK;
 }
 
+PTHR_API pthr_status pthr_reservoir_autocorrelation_noalloc(pthr_batch *b, int first, int count, int n_points,
+                                                            int sweeps_per_point, int64_t *out_device) {
+    if (!b) return fail(nullptr, PTHR_E_INVAL, "NULL handle");
+    if (b->cfg.n_res < 1) return fail(b, PTHR_E_INVAL, "the batch has no reservoir clones");
+    if (first < 0 || count < 1 || first + count > b->cfg.n_samples || n_points < 1 || sweeps_per_point < 1 ||
+        !out_device)
+        return fail(b, PTHR_E_INVAL, "bad sample range, point count, sweeps or NULL output");
+    const size_t need = (size_t)count * b->cfg.n_replicas * b->cfg.n_res * (size_t)lattice_words(b->cfg.L) * 4;
+    cudaPointerAttributes pa{};
+    int dev = 0;
+    CUDA_TRY(b, cudaPointerGetAttributes(&pa, b->ws), "workspace attributes");
+    CUDA_TRY(b, cudaGetDevice(&dev), "current device");
+    if (pa.type == cudaMemoryTypeDevice && pa.device != dev)
+        return fail(b, PTHR_E_INVAL, "make the batch's device (%d) current first (current: %d)", pa.device, dev);
+    void *snap = nullptr;
+    size_t cap = 0;
+    CUDA_TRY(b, noalloc_snapshot(&snap, &cap), "fixed snapshot address");
+    if (need > cap)
+        return fail(b, PTHR_E_NOMEM,
+                    "the reservoir snapshot of %d samples needs %zu bytes; the fixed scratch holds %zu "
+                    "(call it on fewer samples at a time)", count, need, cap);
+    return pthr_reservoir_autocorrelation(b, first, count, n_points, sweeps_per_point, snap, cap, out_device);
+}
+
 PTHR_API pthr_status pthr_check_canaries(pthr_batch *b, int *bad_buffer) {
     if (!b) return fail(nullptr, PTHR_E_INVAL, "NULL handle");
     const Layout l = make_layout(&b->cfg);

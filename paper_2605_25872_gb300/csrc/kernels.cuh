@@ -51,6 +51,7 @@ cudaError_t launch_import_spins(const Batch &b, const int8_t *in, cudaStream_t s
 cudaError_t launch_snapshot_reservoir(const Batch &b, int first, int count, uint32_t *snap, cudaStream_t st);
 cudaError_t launch_reservoir_overlap(const Batch &b, int first, int count, const uint32_t *snap,
                                      long long *out, int n_points, int point, cudaStream_t st);
+cudaError_t noalloc_snapshot(void **ptr, size_t *bytes);   // fixed device scratch, per device
 
 // peaks.cu
 constexpr int PEAK_SINK_BYTES = 4096;   // scratch words the microbenchmarks may store to
