@@ -147,6 +147,50 @@ def kernel_counters():
     return c if c.get("kernel_version") == kernel_version() else None
 
 
+def sweep_roofline(n_sm, mhz, upd_per_s, measured):
+    """Roofline of the sweep kernel, the dominant kernel of the EMCS.
+
+    It is bound by the ALU pipe (integer logic: spin decodes, Philox XORs,
+    mask assembly): the ncu count of ALU-pipe thread-instructions per update
+    times the updates/s of the live sweep launch, over 64 ALU lanes/clk/SM at
+    the median SM clock of the timed region (the lane count is confirmed by
+    the lop3 microbenchmark).  Beside it: the issue fraction (all
+    thread-instructions over 128/clk/SM), the algorithmic 29 ops/update, and
+    the shared-memory fraction against the measured load bandwidth."""
+    cnt = kernel_counters()
+    alu_peak = n_sm * 64 * mhz * 1e6
+    issue_peak = n_sm * 128 * mhz * 1e6
+    alg = OPS_PER_UPDATE * upd_per_s
+    roof = {"kernel": f"sweep_kernel<{WL.L}, Metropolis>", "bound": "alu"}
+    if cnt:
+        alu = cnt["alu_inst_per_update"] * upd_per_s
+        roof.update({"achieved": alu / 1e12, "peak": alu_peak / 1e12, "unit": "T thread-instr/s (ALU pipe)",
+                     "frac": alu / alu_peak, "traffic": cnt.get("dram_bytes_per_launch"),
+                     "basis": (f"ncu: {cnt['alu_inst_per_update']:.2f} ALU-pipe thread-instructions per "
+                               f"spin update x updates/s of the sweep launch (CUDA events), over {n_sm} SMs "
+                               f"x 64 ALU lanes/clk x {mhz:.0f} MHz (median SM clock of the timed region)"),
+                     "issue": {"achieved": cnt["inst_per_update"] * upd_per_s / 1e12, "peak": issue_peak / 1e12,
+                               "frac": cnt["inst_per_update"] * upd_per_s / issue_peak,
+                               "inst_per_update": cnt["inst_per_update"],
+                               "basis": "all thread-instructions over 128/clk/SM"}})
+    else:
+        roof.update({"achieved": alg / 1e12, "peak": issue_peak / 1e12, "unit": "T lane-ops/s",
+                     "frac": alg / issue_peak, "traffic": None,
+                     "basis": (f"no ncu counters for this kernel source: algorithmic {OPS_PER_UPDATE} ops "
+                               f"per update over {n_sm} SMs x 128 lanes x {mhz:.0f} MHz")})
+    roof["algorithmic"] = {"ops_per_update": OPS_PER_UPDATE, "achieved": alg / 1e12,
+                           "frac_of_issue_peak": alg / issue_peak}
+    if measured:
+        smem = SMEM_BYTES_PER_UPDATE * upd_per_s
+        roof["alu_peak_measured"] = measured["alu_inst_per_s"] / 1e12
+        roof["smem"] = {"achieved_TBps": smem / 1e12, "peak_TBps": measured["smem_read_Bps"] / 1e12,
+                        "frac": smem / measured["smem_read_Bps"], "bytes_per_update": SMEM_BYTES_PER_UPDATE,
+                        "peak_basis": "measured 16-byte shared loads (pthr_measure_peak)",
+                        "half_of_smem_roofline_reached": smem >= 0.5 * measured["smem_read_Bps"]}
+        roof["l2_peak_TBps"] = measured["l2_read_Bps"] / 1e12
+    return roof
+
+
 def batch_config(n_samples=None):
     from paper_2605_25872_gb300 import BatchConfig
     return BatchConfig(L=WL.L, n_samples=n_samples or WL.n_samples, n_temps=WL.n_temps,
@@ -347,49 +391,27 @@ def run_gpu(args):
         n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
         mhz = clocks.get("sm_mhz") or float(pk.get("sm_max_mhz", 2070.0))
         upd_per_s = upd / (ms_sweep * 1e-3)
-        # issue roofline of the sweep kernel: thread-instructions per update
-        # (ncu) x updates/s over 128 thread-instructions/clk/SM at the median
-        # SM clock of the timed region
-        issue_peak = n_sm * 128 * mhz * 1e6 / 1e12                    # T thread-instr/s
-        cnt = kernel_counters()
-        inst = cnt["inst_per_update"] if cnt else None
-        traffic = cnt.get("dram_bytes_per_launch") if cnt else None
-        achieved_inst = (inst * upd_per_s / 1e12) if inst else None
-        alg = OPS_PER_UPDATE * upd_per_s / 1e12
-        smem_achieved = SMEM_BYTES_PER_UPDATE * upd_per_s
-        roof = {"kernel": f"sweep_kernel<{WL.L}, Metropolis>", "bound": "alu",
-                "achieved": achieved_inst if inst else alg, "peak": issue_peak,
-                "unit": "T thread-instr/s",
-                "frac": (achieved_inst if inst else alg) / issue_peak, "traffic": traffic,
-                "basis": (f"ncu: {inst:.2f} thread-instructions per spin update (all pipes) x "
-                          f"updates/s in the sweep launch (CUDA events), over {n_sm} SMs x 128 "
-                          f"thread-instr/clk x {mhz:.0f} MHz (median SM clock of the timed region)")
-                if inst else (f"no ncu counters for this kernel source: algorithmic {OPS_PER_UPDATE} "
-                              f"ALU ops per update over {n_sm} SMs x 128 lanes x {mhz:.0f} MHz"),
-                "algorithmic_ops_per_update": OPS_PER_UPDATE,
-                "algorithmic_frac": alg / issue_peak}
-        if measured:
-            if cnt and cnt.get("alu_inst_per_update"):
-                a = cnt["alu_inst_per_update"] * upd_per_s
-                roof["alu_pipe"] = {"achieved": a / 1e12, "peak": measured["alu_inst_per_s"] / 1e12,
-                                    "unit": "T thread-instr/s", "frac": a / measured["alu_inst_per_s"],
-                                    "inst_per_update": cnt["alu_inst_per_update"],
-                                    "peak_basis": "measured lop3 issue rate (pthr_measure_peak)"}
-            roof["smem"] = {"achieved_TBps": smem_achieved / 1e12,
-                            "peak_TBps": measured["smem_read_Bps"] / 1e12,
-                            "frac": smem_achieved / measured["smem_read_Bps"],
-                            "bytes_per_update": SMEM_BYTES_PER_UPDATE,
-                            "peak_basis": "measured 16-byte shared loads (pthr_measure_peak)",
-                            "target_half_of_smem_roofline_met": smem_achieved >= 0.5 * measured["smem_read_Bps"]}
-            roof["l2_peak_TBps"] = measured["l2_read_Bps"] / 1e12
+        roof = sweep_roofline(n_sm, mhz, upd_per_s, measured)
         pairs = S * (WL.n_replicas // 2) * n_acu_temps()
         ms_cluster = float(phase[:, 1].mean())
         plain = plain_form(dev, upd / S, seeds, J)
         e2e = end_to_end(dev, cfg, J, seeds, args.steps)
-        serving = None
+        autocorr = None
+        if WL.er_on and world == 1:
+            # reservoir residence calibration (Sec. 3, ER): C(tau) at T_max for
+            # tau = 240, 480, 720, 960 sweeps over every reservoir clone
+            from paper_2605_25872_gb300.analysis import spin_autocorrelation
+            sums = b.reservoir_autocorrelation(4, WL.res_sweeps_per_emcs).cpu().numpy()
+            _, cmean, cerr = spin_autocorrelation(sums, WL.n_replicas, WL.n_res, WL.V)
+            autocorr = {"tau_sweeps": [WL.res_sweeps_per_emcs * (p + 1) for p in range(4)],
+                        "C": [float(x) for x in cmean], "C_err": [float(x) for x in cerr],
+                        "samples": S, "clones_per_sample": WL.n_replicas * WL.n_res,
+                        "paper": "C(960) < 1e-3 (Sec. 3, ER)"}
+        serving = mixed = None
         if WL is W.WORKLOADS["c4"] and world == 1:
             serving = serve_measure(args.serve_budget, args.serve_requests, args.serve_mem_gb,
                                     args.serve_max_slots, args.serve_chunk)
+            mixed = mixed_group_measure(dev)
         result = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
@@ -408,6 +430,8 @@ def run_gpu(args):
             "measured_peaks": {k: v for k, v in measured.items()} if measured else None,
             "gpu_launches": 4 * args.steps,
             "serving": serving,
+            "mixed_sizes": mixed,
+            "reservoir_autocorrelation": autocorr,
             "cpu_baseline": cpu_baseline(),
             "e2e": e2e,
             "clocks": clocks,
@@ -531,6 +555,54 @@ def serve_measure(budget, n_req, mem_gb, max_slots, max_chunk):
                                    "4 reservoir clones, paper EMCS, couplings drawn on the device from each "
                                    "request's seed, 960-sweep reservoir pre-thermalisation at admission, "
                                    "Poisson arrivals at 0.8 x the measured capacity"}}
+
+
+def mixed_group_measure(dev, slots=128, n_emcs=10):
+    """Mixed lattice sizes advanced together: one resident batch per L in
+    {6, 8, 10, 12, 16} (slots samples each, 24 temperatures, 4 replicas + 4
+    reservoir clones, paper EMCS), every slot busy.  Times n_emcs EMCS as one
+    group graph (pthr_group: one launch per EMCS step over every size) and
+    as one graph per batch on its own stream."""
+    import torch
+    from paper_2605_25872_gb300 import Batch, BatchConfig, Group
+    batches = []
+    for L in W.SERVE_SIZES:
+        cfg = BatchConfig(L=L, n_samples=slots, n_temps=24)
+        b = Batch(cfg, couplings=None, seeds=W.sample_seeds(W.batch_seed(5) + 1000 * L, slots), device=dev,
+                  stream=torch.cuda.Stream(dev))
+        b.prethermalize(960)
+        batches.append(b)
+    torch.cuda.synchronize(dev)
+    upd = sum(b.cfg.n_samples * b.cfg.n_replicas * (b.cfg.n_temps * b.cfg.sweeps_per_emcs
+                                                      + b.cfg.n_res * b.cfg.res_sweeps_per_emcs) * b.cfg.V
+              for b in batches)
+    g = Group(batches)
+    g.emcs(2)
+    g.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(g.stream)
+    g.emcs(n_emcs)
+    e1.record(g.stream)
+    g.synchronize()
+    ms_group = e0.elapsed_time(e1) / n_emcs
+    launches = g.launches_per_emcs
+    g.close()
+    for b in batches:
+        b.emcs(1, graph=True)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(n_emcs):
+        for b in batches:
+            b.emcs(1, graph=True)
+    torch.cuda.synchronize(dev)
+    ms_sep = (time.perf_counter() - t0) * 1e3 / n_emcs
+    for b in batches:
+        b.close()
+    return {"sizes": list(W.SERVE_SIZES), "samples_per_size": slots,
+            "group_launches_per_emcs": launches, "group_ms_per_emcs": ms_group,
+            "group_updates_per_ns": upd / (ms_group * 1e6),
+            "separate_graphs_ms_per_emcs": ms_sep, "separate_updates_per_ns": upd / (ms_sep * 1e6),
+            "separate_launches_per_emcs": 4 * len(batches)}
 
 
 def run_serve(args):

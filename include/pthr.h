@@ -273,17 +273,25 @@ PTHR_API pthr_status pthr_reset_samples(pthr_batch *b, int first, int count,
 PTHR_API pthr_status pthr_set_active(pthr_batch *b, int first, int count, int active);
 
 /* Groups: several batches (for instance one per lattice size) advanced
- * together.  pthr_group_create captures one EMCS of every batch -- each on
- * its own stream, forked from and joined to `stream` -- into one CUDA graph;
- * pthr_group_emcs replays it n times on `stream`, so mixed-L work runs as one
- * launch per EMCS with the batches overlapping on the device.  The batches
- * must be at an EMCS boundary, must not be destroyed before the group, and
- * their idle slots cost no work.  Kernel shapes are fixed at creation. */
+ * together by one CUDA graph per EMCS (Sec. 3: the same EMCS for every
+ * sample, whatever its size).  When the batches share an update rule, have
+ * L in {4, 6, 8, 10, 12, 14, 16}, number at most 8 and set no
+ * cluster_iter_cap, the graph holds four launches in all -- the sweep, the
+ * cluster move, the swap and the measurement of every batch, each step one
+ * kernel over the blocks of all batches; otherwise it holds each batch's own
+ * EMCS on its own stream, forked from and joined to `stream`.
+ * pthr_group_emcs replays the graph n times on `stream`.  The batches must be
+ * at an EMCS boundary, must not be destroyed before the group, and their
+ * idle slots cost no work.  Kernel shapes are fixed at creation.  Results
+ * are those of stepping every batch alone. */
 typedef struct pthr_group pthr_group;
 PTHR_API pthr_status pthr_group_create(pthr_batch *const *batches, int n, void *stream,
                                        pthr_group **out);
 PTHR_API pthr_status pthr_group_emcs(pthr_group *g, int n);
 PTHR_API void pthr_group_destroy(pthr_group *g);
+/* Kernel launches per EMCS in the group's graph (4 for the one-launch-per-
+ * step form). */
+PTHR_API pthr_status pthr_group_info(const pthr_group *g, int *launches_per_emcs);
 
 /* Checkpoint: the workspace holds the whole state (counter-based random
  * numbers make resume exact), so a blob is the workspace plus a header.

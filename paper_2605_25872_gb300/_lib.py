@@ -34,7 +34,7 @@ EXPORTS = ("pthr_required_bytes", "pthr_buffer_info", "pthr_lattice_bytes", "pth
            "pthr_reset_samples", "pthr_set_active", "pthr_save", "pthr_load", "pthr_last_error",
            "pthr_version", "pthr_group_create", "pthr_group_emcs", "pthr_group_destroy",
            "pthr_measure_peak", "pthr_check_canaries", "pthr_reservoir_autocorrelation",
-           "pthr_reservoir_autocorrelation_noalloc")
+           "pthr_reservoir_autocorrelation_noalloc", "pthr_group_info")
 PEAK_SMEM_READ, PEAK_L2_READ, PEAK_ALU, PEAK_FMA, PEAK_FMA2, PEAK_FP64 = range(6)
 
 
@@ -105,6 +105,7 @@ def load(path: str | None = None):
         "pthr_check_canaries": [vp, P(ctypes.c_int)],
         "pthr_reservoir_autocorrelation": [vp, i, i, i, i, vp, sz, vp],
         "pthr_reservoir_autocorrelation_noalloc": [vp, i, i, i, i, vp],
+        "pthr_group_info": [vp, P(i)],
     }
     for name, args in sig.items():
         f = getattr(L, name)

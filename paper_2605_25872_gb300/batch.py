@@ -342,6 +342,12 @@ class Group:
     def emcs(self, n: int = 1):
         check(self.lib.pthr_group_emcs(self.h, n))
 
+    @property
+    def launches_per_emcs(self) -> int:
+        n = ctypes.c_int(0)
+        check(self.lib.pthr_group_info(self.h, ctypes.byref(n)))
+        return n.value
+
     def reservoir_autocorrelation(self, n_points: int, sweeps_per_point: int, first: int = 0,
                                   count: int | None = None) -> torch.Tensor:
         """Integer sums of s_i(t) s_i(t + tau) over every reservoir clone and

@@ -21,7 +21,8 @@ LIB = os.path.join(BUILD, "libpthr.so")
 BUILD_DEBUG = os.path.join(HERE, "_build_debug")
 LIB_DEBUG = os.path.join(BUILD_DEBUG, "libpthr.so")
 SOURCES = ["capi.cu", "sweep.cu", "sweep_inst_metro_a.cu", "sweep_inst_metro_b.cu",
-           "sweep_inst_hb.cu", "sweep_inst_micsa.cu", "cluster.cu", "exchange.cu", "init.cu", "peaks.cu", "autocorr.cu"]
+           "sweep_inst_hb.cu", "sweep_inst_micsa.cu", "cluster.cu", "exchange.cu", "init.cu", "peaks.cu", "autocorr.cu",
+           "group_sweep.cu", "group_sweep_metropolis.cu", "group_sweep_heatbath.cu", "group_sweep_micsa.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -160,7 +160,9 @@ int default_k(const pthr_config *c, int total_entries) {
     return (int)k;
 }
 
-SweepShape sweep_shape(const pthr_batch *b) {
+// forced_kt > 0: lattices per thread fixed (the mixed-L group sweep compiles
+// one value per lattice size); the lattices per block then follow from it.
+SweepShape sweep_shape(const pthr_batch *b, int forced_kt = 0) {
     const pthr_config *c = &b->cfg;
     SweepShape sh{};
     const int npt = c->n_replicas * c->n_temps;
@@ -187,6 +189,7 @@ SweepShape sweep_shape(const pthr_batch *b) {
     int KT = opts[nopt - 1];
     for (int i = 0; i < nopt; ++i)
         if (opts[i] >= need) { KT = opts[i]; break; }
+    if (forced_kt > 0) KT = forced_kt;
     if (P0 * KT < Kmax) {            // largest variant too small: fewer lattices per block
         if (sh.K_pt > P0 * KT) sh.K_pt = P0 * KT;
         if (sh.K_res > P0 * KT) sh.K_res = P0 * KT;
@@ -200,9 +203,13 @@ SweepShape sweep_shape(const pthr_batch *b) {
     return sh;
 }
 
-pthr_status do_sweep(pthr_batch *b, int n_pt, int n_res, int first, int count, int pretherm) {
+struct SweepLaunch { SweepArgs a; int blocks, threads, KT; size_t smem; };
+
+// Arguments and shape of one sweep launch (blocks == 0: nothing to do).
+pthr_status sweep_launch(pthr_batch *b, int n_pt, int n_res, int first, int count, int pretherm,
+                         int forced_kt, SweepLaunch *out) {
     const pthr_config *c = &b->cfg;
-    SweepShape sh = sweep_shape(b);
+    SweepShape sh = sweep_shape(b, forced_kt);
     SweepArgs a{};
     a.b = b->dev;
     a.n_pt_sweeps = n_pt;
@@ -219,12 +226,23 @@ pthr_status do_sweep(pthr_batch *b, int n_pt, int n_res, int first, int count, i
     a.sample_count = count;
     a.emcs_override = pretherm;
     a.Gt = sh.Gt;
-    const int blocks = count * ((a.do_res ? sh.res_tasks : 0) + (a.do_pt ? sh.pt_tasks : 0));
-    if (blocks == 0) return PTHR_OK;
-    const size_t smem = sweep_smem_bytes_for(c->L, sh.K_pt > sh.K_res ? sh.K_pt : sh.K_res);
-    if (smem > 220 * 1024)
-        return fail(b, PTHR_E_INVAL, "sweep block needs %zu bytes of shared memory; lower the lattices per block", smem);
-    CUDA_TRY(b, launch_sweep(a, blocks, sh.threads, sh.KT, b->stream), "sweep launch");
+    out->a = a;
+    out->blocks = count * ((a.do_res ? sh.res_tasks : 0) + (a.do_pt ? sh.pt_tasks : 0));
+    out->threads = sh.threads;
+    out->KT = sh.KT;
+    out->smem = sweep_smem_bytes_for(c->L, sh.K_pt > sh.K_res ? sh.K_pt : sh.K_res);
+    if (out->smem > 220 * 1024)
+        return fail(b, PTHR_E_INVAL, "sweep block needs %zu bytes of shared memory; lower the lattices per block",
+                    out->smem);
+    return PTHR_OK;
+}
+
+pthr_status do_sweep(pthr_batch *b, int n_pt, int n_res, int first, int count, int pretherm) {
+    SweepLaunch sl{};
+    pthr_status st = sweep_launch(b, n_pt, n_res, first, count, pretherm, 0, &sl);
+    if (st != PTHR_OK) return st;
+    if (sl.blocks == 0) return PTHR_OK;
+    CUDA_TRY(b, launch_sweep(sl.a, sl.blocks, sl.threads, sl.KT, b->stream), "sweep launch");
     if (pretherm)   // the next pre-thermalisation sweeps continue the index
         CUDA_TRY(b, launch_advance_pretherm(b->dev, first, count, n_res, b->stream), "pretherm counter");
     return PTHR_OK;
@@ -235,6 +253,14 @@ int default_cluster_threads(int L) {
     const int V = L * L * L;
     int t = ((V / 8 + 31) / 32) * 32;
     return t < 128 ? 128 : (t > 512 ? 512 : t);
+}
+
+int cluster_threads_of(const pthr_batch *b) {
+    int threads = b->tuning.cluster_threads > 0 ? b->tuning.cluster_threads : default_cluster_threads(b->cfg.L);
+    const int V = b->cfg.L * b->cfg.L * b->cfg.L;
+    if (threads > ((V + 31) / 32) * 32) threads = ((V + 31) / 32) * 32;
+    if (threads < 32) threads = 32;
+    return (threads / 32) * 32;
 }
 
 pthr_status do_cluster(pthr_batch *b, int label_only, int32_t *labels) {
@@ -683,7 +709,92 @@ struct pthr_group {
     cudaGraph_t graph;
     cudaGraphExec_t exec;
     int n;
+    int launches;   // kernel launches per EMCS in the graph
 };
+
+namespace {
+
+// One EMCS of every batch as four launches in total (sweep, cluster move,
+// swap, measurement), each over the blocks of all batches; possible when
+// the batches share an update rule, their sizes are compiled into the group
+// kernels and no error-path knob is set.  Returns PTHR_E_STATE (nothing
+// enqueued) when the group does not qualify.
+pthr_status group_fused_emcs(pthr_batch *const *batches, int n, cudaStream_t st, int *launches) {
+    if (n > GROUP_MAX) return PTHR_E_STATE;
+    const int rule = batches[0]->cfg.update_rule;
+    for (int i = 0; i < n; ++i) {
+        const pthr_batch *b = batches[i];
+        if (b->cfg.update_rule != rule || !group_supports_L(b->cfg.L) || b->tuning.cluster_iter_cap > 0 ||
+            b->cfg.n_replicas > 32)
+            return PTHR_E_STATE;
+    }
+    // heaviest batches first
+    int order[GROUP_MAX];
+    for (int i = 0; i < n; ++i) order[i] = i;
+    for (int i = 1; i < n; ++i)
+        for (int j = i; j > 0 && batches[order[j]]->cfg.L > batches[order[j - 1]]->cfg.L; --j) {
+            const int t = order[j]; order[j] = order[j - 1]; order[j - 1] = t;
+        }
+    GroupSweepArgs gs{};
+    GroupClusterArgs gc{};
+    GroupBatchArgs gw{}, gm{};
+    int sw_threads = 32, cl_threads = 32, sw_blocks = 0, cl_blocks = 0, w_blocks = 0, m_blocks = 0, w_threads = 32;
+    size_t sw_smem = 0, cl_smem = 0, w_smem = 0, m_smem = 0;
+    for (int ii = 0; ii < n; ++ii) {
+        pthr_batch *b = batches[order[ii]];
+        const pthr_config *c = &b->cfg;
+        SweepLaunch sl{};
+        if (sweep_launch(b, c->sweeps_per_emcs, c->er_on ? c->res_sweeps_per_emcs : 0, 0, c->n_samples, 0,
+                         group_sweep_kt(c->L), &sl) != PTHR_OK)
+            return PTHR_E_STATE;
+        gs.a[gs.n] = sl.a;
+        gs.off[gs.n] = sw_blocks;
+        ++gs.n;
+        sw_blocks += sl.blocks;
+        if (sl.threads > sw_threads) sw_threads = sl.threads;
+        if (sl.smem > sw_smem) sw_smem = sl.smem;
+        if (c->cluster_mode != PTHR_CLUSTER_OFF && b->dev.n_acu > 0) {
+            ClusterArgs a{};
+            a.b = b->dev;
+            a.sample_first = 0;
+            a.sample_count = c->n_samples;
+            a.iter_cap = 0;
+            gc.a[gc.n] = a;
+            gc.off[gc.n] = cl_blocks;
+            ++gc.n;
+            cl_blocks += c->n_samples * b->dev.NPAIR * b->dev.n_acu;
+            const int t = cluster_threads_of(b);
+            if (t > cl_threads) cl_threads = t;
+            if (cluster_smem_bytes_for(c->L) > cl_smem) cl_smem = cluster_smem_bytes_for(c->L);
+        }
+        gw.b[gw.n] = b->dev;
+        gw.flags[gw.n] = PTHR_SWAP_PT | (c->er_on ? PTHR_SWAP_ER : 0);
+        gw.off[gw.n] = w_blocks;
+        ++gw.n;
+        w_blocks += c->n_samples;
+        if (32 * c->n_replicas > w_threads) w_threads = 32 * c->n_replicas;
+        const size_t ws = (size_t)b->dev.NR * b->dev.NSLOT * (sizeof(double) + sizeof(int));
+        if (ws > w_smem) w_smem = ws;
+        gm.b[gm.n] = b->dev;
+        gm.off[gm.n] = m_blocks;
+        ++gm.n;
+        m_blocks += (c->n_samples * c->n_temps + 7) / 8;
+        if (measure_smem_bytes_for(c->L) > m_smem) m_smem = measure_smem_bytes_for(c->L);
+    }
+    gs.off[gs.n] = sw_blocks;
+    gc.off[gc.n] = cl_blocks;
+    gw.off[gw.n] = w_blocks;
+    gm.off[gm.n] = m_blocks;
+    if (sw_smem > 200 * 1024 || cl_smem > 200 * 1024) return PTHR_E_STATE;
+    if (launch_group_sweep(gs, rule, sw_blocks, sw_threads, sw_smem, st) != cudaSuccess) return PTHR_E_CUDA;
+    if (launch_group_cluster(gc, cl_blocks, cl_threads, cl_smem, st) != cudaSuccess) return PTHR_E_CUDA;
+    if (launch_group_swap(gw, w_blocks, w_threads, w_smem, st) != cudaSuccess) return PTHR_E_CUDA;
+    if (launch_group_measure(gm, m_blocks, m_smem, st) != cudaSuccess) return PTHR_E_CUDA;
+    *launches = (sw_blocks > 0) + (cl_blocks > 0) + (w_blocks > 0) + (m_blocks > 0);
+    return PTHR_OK;
+}
+
+}  // namespace
 
 PTHR_API pthr_status pthr_group_create(pthr_batch *const *batches, int n, void *stream, pthr_group **out) {
     if (!batches || n < 1 || !out || !stream)
@@ -698,6 +809,33 @@ PTHR_API pthr_status pthr_group_create(pthr_batch *const *batches, int n, void *
     }
     cudaStream_t master = (cudaStream_t)stream;
     if (capturing(master)) return fail(nullptr, PTHR_E_STATE, "stream is already capturing");
+    // kernel attributes are set outside the capture (first launch of a kind)
+    {
+        cudaError_t e = cudaStreamBeginCapture(master, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return cuda_fail(nullptr, e, "begin capture");
+        int launches = 0;
+        pthr_status st = group_fused_emcs(batches, n, master, &launches);
+        cudaGraph_t g = nullptr;
+        e = cudaStreamEndCapture(master, &g);
+        if (st == PTHR_OK && e == cudaSuccess) {
+            cudaGraphExec_t exec = nullptr;
+            e = cudaGraphInstantiate(&exec, g, 0);
+            if (e != cudaSuccess) { cudaGraphDestroy(g); return cuda_fail(nullptr, e, "group graph instantiate"); }
+            pthr_group *grp = new pthr_group();
+            grp->stream = master;
+            grp->graph = g;
+            grp->exec = exec;
+            grp->n = n;
+            grp->launches = launches;
+            *out = grp;
+            return PTHR_OK;
+        }
+        if (g) cudaGraphDestroy(g);
+        if (st == PTHR_E_CUDA) return fail(nullptr, st, "group kernel launch failed during capture");
+        if (e != cudaSuccess) return cuda_fail(nullptr, e, "group capture");
+        cudaGetLastError();
+    }
+    // otherwise one EMCS of every batch, each on its own stream, in one graph
     cudaEvent_t fork = nullptr;
     cudaEvent_t *join = new cudaEvent_t[n]();
     cudaError_t e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
@@ -733,7 +871,16 @@ PTHR_API pthr_status pthr_group_create(pthr_batch *const *batches, int n, void *
     grp->graph = g;
     grp->exec = exec;
     grp->n = n;
+    grp->launches = 0;
+    for (int i = 0; i < n; ++i)
+        grp->launches += 2 + (batches[i]->cfg.cluster_mode != PTHR_CLUSTER_OFF && batches[i]->dev.n_acu > 0) + 1;
     *out = grp;
+    return PTHR_OK;
+}
+
+PTHR_API pthr_status pthr_group_info(const pthr_group *g, int *launches_per_emcs) {
+    if (!g || !launches_per_emcs) return fail(nullptr, PTHR_E_INVAL, "NULL group or output");
+    *launches_per_emcs = g->launches;
     return PTHR_OK;
 }
 

@@ -19,7 +19,7 @@
 // H_a + H_b) and the pair is written back.  Every loop is bounded; hitting a bound sets STATUS_NOCONVERGE
 // instead of spinning.
 #include "kernels.cuh"
-#include "geometry.cuh"
+#include "bitrows.cuh"
 
 namespace pthr {
 
@@ -54,36 +54,7 @@ __device__ __forceinline__ void unite(volatile int *parent, int a, int b, int ca
     ok = false;
 }
 
-// bit m of v -> bit 2m (m < 16)
-__device__ __forceinline__ uint32_t spread_bits(uint32_t v) {
-    v = (v | (v << 8)) & 0x00FF00FFu;
-    v = (v | (v << 4)) & 0x0F0F0F0Fu;
-    v = (v | (v << 2)) & 0x33333333u;
-    v = (v | (v << 1)) & 0x55555555u;
-    return v;
-}
-
-// bit 2m of v -> bit m
-__device__ __forceinline__ uint32_t compact_bits(uint32_t v) {
-    v &= 0x55555555u;
-    v = (v | (v >> 1)) & 0x33333333u;
-    v = (v | (v >> 2)) & 0x0F0F0F0Fu;
-    v = (v | (v >> 4)) & 0x00FF00FFu;
-    v = (v | (v >> 8)) & 0x0000FFFFu;
-    return v;
-}
-
-// bit 7 of the four bytes of w (the sign of a packed spin, or where two
-// packed words differ) as the low four bits; a multiply gathers them
-__device__ __forceinline__ uint32_t sign_nibble(uint32_t w) {
-    return ((w & 0x80808080u) * 0x00204081u) >> 28;
-}
-
-// L-bit row rotated so that bit x holds bit (x + 1) mod L
-template <int L>
-__device__ __forceinline__ uint32_t rot_next(uint32_t v) {
-    return (v >> 1) | ((v & 1u) << (L - 1));
-}
+// compact_bits, spread_bits, sign_nibble and rot_next: geometry.cuh
 
 // natural site index of byte kk of packed word w
 template <int L>
@@ -148,10 +119,9 @@ __device__ __forceinline__ void clone_energy_pairs(const uint32_t *S, const floa
 // slower).  CAPPED = true: the bound comes from the tuning knob, used only to
 // exercise the error path.
 template <int L, bool CAPPED>
-__global__ void __launch_bounds__(512, 4) cluster_kernel(ClusterArgs a) {
+__device__ __forceinline__ void cluster_block(const ClusterArgs &a, int bid, unsigned char *smem) {
     using Gm = Geom<L>;
     constexpr int V = Gm::V, LW = Gm::LAT_WORDS, W = Gm::W, Lh = Gm::Lh;
-    extern __shared__ __align__(16) unsigned char smem[];
     int *parent = reinterpret_cast<int *>(smem);                       // [V]
     int *cnt = parent + V;                                             // [V]
     uint32_t *sa = reinterpret_cast<uint32_t *>(cnt + V);              // [LW]
@@ -160,16 +130,16 @@ __global__ void __launch_bounds__(512, 4) cluster_kernel(ClusterArgs a) {
     uint32_t *qrow = reinterpret_cast<uint32_t *>(flag + ((V + 3) & ~3));  // [L*L] q bits per x row,
                                                                            // later the flip bits
     uint32_t *arow = qrow + L * L;                                     // [L*L] clone a: 1 = spin -1
+    int *s_scan = reinterpret_cast<int *>(arow + L * L);               // [blockDim.x] row-count scan
     __shared__ int s_ok;
     __shared__ int s_nneg, s_root, s_nclus, s_nflip;
     __shared__ int s_top[2][32];
     __shared__ double s_E[2];
     __shared__ unsigned long long s_Ei[1];
-    __shared__ int s_scan[1024];
 
     const Batch &b = a.b;
     const int n_acu = b.n_acu;
-    int t = blockIdx.x;
+    int t = bid;
     const int k = t % n_acu; t /= n_acu;
     const int P = t % b.NPAIR; t /= b.NPAIR;
     const int s = a.sample_first + t;
@@ -448,11 +418,19 @@ __global__ void __launch_bounds__(512, 4) cluster_kernel(ClusterArgs a) {
     }
 }
 
+template <int L, bool CAPPED>
+__global__ void __launch_bounds__(512, 4) cluster_kernel(ClusterArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    cluster_block<L, CAPPED>(a, blockIdx.x, smem);
+}
+
+// parent, cnt [V] int; both clones [LW]; root flags [V] bytes; q and clone-a
+// rows [L*L]; the row-count scan of the single-cluster move [<= 1024] int
 template <int L>
 size_t cluster_smem(void) {
     using Gm = Geom<L>;
     return (size_t)8 * Gm::V + (size_t)8 * Gm::LAT_WORDS + (size_t)((Gm::V + 3) & ~3) +
-           (size_t)8 * L * L + 16;
+           (size_t)8 * L * L + (size_t)4 * 1024 + 16;
 }
 
 template <int L>
@@ -473,7 +451,42 @@ cudaError_t launch_cluster_L(const ClusterArgs &a, int threads, cudaStream_t st)
     return cudaGetLastError();
 }
 
+// The cluster step of a mixed-L group (see kernels.cuh): the blocks of every
+// batch's cluster launch, dispatching on its lattice size; block size = the
+// largest of the group (every loop strides by the block size).
+__global__ void __launch_bounds__(512, 2) group_cluster_kernel(GroupClusterArgs g) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ ClusterArgs ca;
+    const int i = group_member(g.off, g.n, (int)blockIdx.x);
+    if (threadIdx.x == 0) {
+        switch (i) {
+#define PICK(J) case J: ca = g.a[J]; break;
+            PICK(0) PICK(1) PICK(2) PICK(3) PICK(4) PICK(5) PICK(6) PICK(7)
+#undef PICK
+        }
+    }
+    __syncthreads();
+    const int bid = (int)blockIdx.x - g.off[i];
+    switch (ca.b.L) {
+#define X(LL) case LL: cluster_block<LL, false>(ca, bid, smem); break;
+        X(4) X(6) X(8) X(10) X(12) X(14) X(16)
+#undef X
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_group_cluster(const GroupClusterArgs &g, int blocks, int threads, size_t smem, cudaStream_t st) {
+    if (blocks <= 0) return cudaSuccess;
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = allow_max_dynamic_smem(group_cluster_kernel);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    group_cluster_kernel<<<blocks, threads, smem, st>>>(g);
+    return cudaGetLastError();
+}
 
 size_t cluster_smem_bytes_for(int L) {
 #define X(LL) if (L == LL) return cluster_smem<LL>();

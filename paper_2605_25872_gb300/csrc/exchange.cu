@@ -7,7 +7,7 @@
 // the clone that reached T_min, exchanges the clone at T_max with the oldest
 // reservoir clone, and finally the block advances the sample's EMCS counter.
 #include "kernels.cuh"
-#include "geometry.cuh"
+#include "bitrows.cuh"
 
 namespace pthr {
 
@@ -15,11 +15,12 @@ namespace {
 
 constexpr int MAX_SLOT = 256;
 
-__global__ void swap_kernel(Batch b, int flags, int first) {
-    const int s = first + blockIdx.x;
+// One block of the swap launch (block bid = sample first + bid); warps past
+// the batch's groups only take part in the barrier.
+__device__ __forceinline__ void swap_block(const Batch &b, int flags, int first, int bid, unsigned char *smem) {
+    const int s = first + bid;
     if (!b.active[s]) return;
     const int g = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    extern __shared__ __align__(16) unsigned char smem[];
     double *s_E = reinterpret_cast<double *>(smem);                    // [NR][NSLOT]
     int *s_perm = reinterpret_cast<int *>(s_E + b.NR * b.NSLOT);       // [NR][NSLOT]
     const uint32_t emcs = b.emcs[s];
@@ -82,33 +83,9 @@ __global__ void swap_kernel(Batch b, int flags, int first) {
     if (threadIdx.x == 0) b.emcs[s] = emcs + 1u;
 }
 
-// Overlap counts of clones A and B on the packed colour-row layout: nneg =
-// number of sites with q_i = -1, ndiff = number of forward links (i, i+mu)
-// with q_i != q_{i+mu}.  One 32-bit word holds four same-colour sites; the
-// XOR of the two clones' words has bit 7 of a byte set where q_i = -1, and
-// each word is compared with the words of its +x, +y, +z neighbours (the
-// same words the sweep reads).
-template <int L>
-__device__ __forceinline__ void overlap_counts(const uint32_t *A, const uint32_t *B, int tid,
-                                               int T, int &nneg, int &ndiff) {
-    using Gm = Geom<L>;
-    constexpr int W = Gm::W, ROWS = Gm::ROWS;
-    nneg = 0;
-    ndiff = 0;
-    for (int w = tid; w < Gm::LAT_WORDS; w += T) {
-        const int c = w / (ROWS * W);
-        const int g = w - c * ROWS * W;
-        const GroupGeo q = group_geo<L>(g, c);
-        const uint32_t vm = valid_mask<L>(g % W);
-        const uint32_t qw = (A[q.own] ^ B[q.own]) & vm;
-        const uint32_t xa = A[q.xa] ^ B[q.xa];
-        const uint32_t xs = __byte_perm(A[q.wA] ^ B[q.wA], A[q.wB] ^ B[q.wB], q.selx);
-        const uint32_t qxp = q.par ? xs : xa;
-        const uint32_t qyp = A[q.yp] ^ B[q.yp];
-        const uint32_t qzp = A[q.zp] ^ B[q.zp];
-        nneg += __popc(qw);
-        ndiff += __popc((qw ^ qxp) & vm) + __popc((qw ^ qyp) & vm) + __popc((qw ^ qzp) & vm);
-    }
+__global__ void swap_kernel(Batch b, int flags, int first) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    swap_block(b, flags, first, blockIdx.x, smem);
 }
 
 constexpr int MEASURE_WARPS = 8;   // (sample, temperature) items per measurement block
@@ -117,38 +94,56 @@ constexpr int MEASURE_WARPS = 8;   // (sample, temperature) items per measuremen
 // layout per (s, k): [0] measurements, [1] sum e, [2] sum e^2 (over groups),
 // [3] sum q, [4] sum q^2, [5] sum q_l, [6] sum S, [7] sum q^4 (over pairs).
 //
-// The warp counts the overlaps of every replica pair (and the chaos pair);
-// lane P keeps pair P's counts.  Then the FP64 quantities of the groups and
-// pairs are evaluated on separate lanes, and lane 0 adds them to the
-// accumulators in the fixed order (groups, then pairs) with one IEEE
-// rounding per operation.  No shared memory and no block barrier.
+// For every replica pair the warp builds the q rows of the two clones (one
+// L-bit mask per natural x row, bit x set where q_i = -1; each packed word is
+// read once, row by row, so a warp's loads are consecutive words) into its
+// shared-memory slot, then counts the sites with q_i = -1 and the forward
+// links (i, i + mu) with q_i != q_{i+mu} by popcounts of each row against
+// its rotation (x), its y + 1 row and its z + 1 row.  Lane P keeps pair P's
+// counts.  Then the FP64 quantities of the groups and pairs are evaluated on
+// separate lanes, and lane 0 adds them to the accumulators in the fixed
+// order (groups, then pairs) with one IEEE rounding per operation.
 template <int L>
-__global__ void __launch_bounds__(32 * MEASURE_WARPS) measure_kernel(Batch b, int first, int count,
-                                                                     int chaos) {
+__device__ __forceinline__ void measure_block(const Batch &b, int first, int count, int chaos, int bid,
+                                              unsigned char *smem) {
     using Gm = Geom<L>;
-    constexpr int V = Gm::V, LW = Gm::LAT_WORDS;
-    const int lane = threadIdx.x & 31;
-    const int item = blockIdx.x * MEASURE_WARPS + (threadIdx.x >> 5);
+    constexpr int V = Gm::V, LW = Gm::LAT_WORDS, ROWS = Gm::ROWS;
+    uint32_t *s_q = reinterpret_cast<uint32_t *>(smem);   // [MEASURE_WARPS][ROWS]
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int item = bid * MEASURE_WARPS + wid;
     if (item >= count * b.NT) return;                 // warp-uniform
     const int s = first + item / b.NT, k = item % b.NT;
     if (!PTHR_DCHECK(b.status, s >= 0 && s < b.S)) return;
     if (!b.active[s]) return;
     const int32_t *perm = b.perm + (size_t)s * b.NR * b.NSLOT;
     const uint32_t *spins = b.spins + (size_t)s * b.NLAT * LW;
+    uint32_t *qr = s_q + wid * ROWS;
     int tn = 0, td = 0, tc = 0;                       // pair `lane`'s counts
     for (int P = 0; P < b.NPAIR; ++P) {
         const int la = 2 * P * b.NSLOT + perm[2 * P * b.NSLOT + k];
         const int lb = (2 * P + 1) * b.NSLOT + perm[(2 * P + 1) * b.NSLOT + k];
         if (!PTHR_DCHECK(b.status, la >= 2 * P * b.NSLOT && la < (2 * P + 1) * b.NSLOT &&
                                     lb >= (2 * P + 1) * b.NSLOT && lb < (2 * P + 2) * b.NSLOT)) return;
-        int nneg, ndiff, cneg = 0;
-        overlap_counts<L>(spins + (size_t)la * LW, spins + (size_t)lb * LW, lane, 32, nneg, ndiff);
+        const uint32_t *A = spins + (size_t)la * LW, *B = spins + (size_t)lb * LW;
+        int nneg = 0, ndiff = 0, cneg = 0;
+        for (int r = lane; r < ROWS; r += 32) {
+            const uint32_t q = diff_row<L>(A, B, r);
+            qr[r] = q;
+            nneg += __popc(q);
+        }
+        __syncwarp();
+        for (int r = lane; r < ROWS; r += 32) {
+            const int y = r % L, z = r / L;
+            const uint32_t q = qr[r];
+            const uint32_t qy = qr[((y + 1) % L) + L * z], qz = qr[y + L * ((z + 1) % L)];
+            ndiff += __popc(q ^ rot_next<L>(q)) + __popc(q ^ qy) + __popc(q ^ qz);
+        }
         if (chaos) {
             // temperature chaos: clone of group 2P at T_0 against group 2P+1 at T_k
-            const int l0 = 2 * P * b.NSLOT + perm[2 * P * b.NSLOT];
-            int cdiff;
-            overlap_counts<L>(spins + (size_t)l0 * LW, spins + (size_t)lb * LW, lane, 32, cneg, cdiff);
+            const uint32_t *A0 = spins + (size_t)(2 * P * b.NSLOT + perm[2 * P * b.NSLOT]) * LW;
+            for (int r = lane; r < ROWS; r += 32) cneg += __popc(diff_row<L>(A0, B, r));
         }
+        __syncwarp();                                 // qr is reused by the next pair
         nneg = __reduce_add_sync(0xffffffffu, nneg);
         ndiff = __reduce_add_sync(0xffffffffu, ndiff);
         cneg = __reduce_add_sync(0xffffffffu, cneg);
@@ -209,7 +204,71 @@ __global__ void __launch_bounds__(32 * MEASURE_WARPS) measure_kernel(Batch b, in
     }
 }
 
+template <int L>
+__global__ void __launch_bounds__(32 * MEASURE_WARPS) measure_kernel(Batch b, int first, int count,
+                                                                     int chaos) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    measure_block<L>(b, first, count, chaos, blockIdx.x, smem);
+}
+
+// Swap and measurement steps of a mixed-L group (see kernels.cuh).
+__global__ void group_swap_kernel(GroupBatchArgs g) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ Batch bb;
+    __shared__ int fl;
+    const int i = group_member(g.off, g.n, (int)blockIdx.x);
+    if (threadIdx.x == 0) {
+        switch (i) {
+#define PICK(J) case J: bb = g.b[J]; fl = g.flags[J]; break;
+            PICK(0) PICK(1) PICK(2) PICK(3) PICK(4) PICK(5) PICK(6) PICK(7)
+#undef PICK
+        }
+    }
+    __syncthreads();
+    swap_block(bb, fl, 0, (int)blockIdx.x - g.off[i], smem);
+}
+
+__global__ void __launch_bounds__(32 * MEASURE_WARPS) group_measure_kernel(GroupBatchArgs g) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ Batch bb;
+    const int i = group_member(g.off, g.n, (int)blockIdx.x);
+    if (threadIdx.x == 0) {
+        switch (i) {
+#define PICK(J) case J: bb = g.b[J]; break;
+            PICK(0) PICK(1) PICK(2) PICK(3) PICK(4) PICK(5) PICK(6) PICK(7)
+#undef PICK
+        }
+    }
+    __syncthreads();
+    const int bid = (int)blockIdx.x - g.off[i];
+    switch (bb.L) {
+#define X(LL) case LL: measure_block<LL>(bb, 0, bb.S, 0, bid, smem); break;
+        X(4) X(6) X(8) X(10) X(12) X(14) X(16)
+#undef X
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_group_swap(const GroupBatchArgs &g, int blocks, int threads, size_t smem, cudaStream_t st) {
+    if (blocks <= 0) return cudaSuccess;
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = allow_max_dynamic_smem(group_swap_kernel);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    group_swap_kernel<<<blocks, threads, smem, st>>>(g);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_group_measure(const GroupBatchArgs &g, int blocks, size_t smem, cudaStream_t st) {
+    if (blocks <= 0) return cudaSuccess;
+    group_measure_kernel<<<blocks, 32 * MEASURE_WARPS, smem, st>>>(g);
+    return cudaGetLastError();
+}
+
+size_t measure_smem_bytes_for(int L) { return (size_t)MEASURE_WARPS * L * L * 4; }
 
 cudaError_t launch_swap(const Batch &b, int flags, int first, int count, cudaStream_t st) {
     if (b.NR > 32 || b.NSLOT > MAX_SLOT) return cudaErrorInvalidValue;
@@ -230,7 +289,7 @@ cudaError_t launch_measure(const Batch &b, int first, int count, int chaos, cuda
     if (items <= 0) return cudaSuccess;
     const int blocks = (int)((items + MEASURE_WARPS - 1) / MEASURE_WARPS);
 #define X(LL) if (b.L == LL) { \
-        measure_kernel<LL><<<blocks, 32 * MEASURE_WARPS, 0, st>>>(b, first, count, chaos); \
+        measure_kernel<LL><<<blocks, 32 * MEASURE_WARPS, measure_smem_bytes_for(LL), st>>>(b, first, count, chaos); \
         return cudaGetLastError(); }
     PTHR_FOR_EACH_L(X)
 #undef X

@@ -1,0 +1,11 @@
+// group_sweep_micsa.cu -- the mixed-L group sweep for the micsa rule.
+#include "group_sweep.cuh"
+
+namespace pthr {
+
+cudaError_t launch_group_sweep_micsa(const GroupSweepArgs &g, int blocks, int threads, size_t smem,
+                                       cudaStream_t st) {
+    return launch_group_sweep_rule<PTHR_MICSA>(g, blocks, threads, smem, st);
+}
+
+}  // namespace pthr

@@ -47,6 +47,32 @@ cudaError_t launch_advance_pretherm(const Batch &b, int first, int count, int n_
 cudaError_t launch_export_spins(const Batch &b, int8_t *out, cudaStream_t st);
 cudaError_t launch_import_spins(const Batch &b, const int8_t *in, cudaStream_t st);
 
+// Mixed-L groups: one launch per EMCS step over the blocks of up to
+// GROUP_MAX batches (group_sweep.cuh, cluster.cu, exchange.cu).  Block b of
+// the launch belongs to batch i with off[i] <= b < off[i+1], as its block
+// b - off[i].
+constexpr int GROUP_MAX = 8;
+struct GroupSweepArgs { int n; int off[GROUP_MAX + 1]; SweepArgs a[GROUP_MAX]; };
+struct GroupClusterArgs { int n; int off[GROUP_MAX + 1]; ClusterArgs a[GROUP_MAX]; };
+struct GroupBatchArgs { int n; int off[GROUP_MAX + 1]; int flags[GROUP_MAX]; Batch b[GROUP_MAX]; };
+bool group_supports_L(int L);
+int group_sweep_kt(int L);                 // lattices per thread of the group sweep
+cudaError_t launch_group_sweep(const GroupSweepArgs &g, int rule, int blocks, int threads, size_t smem,
+                               cudaStream_t st);
+cudaError_t launch_group_cluster(const GroupClusterArgs &g, int blocks, int threads, size_t smem, cudaStream_t st);
+cudaError_t launch_group_swap(const GroupBatchArgs &g, int blocks, int threads, size_t smem, cudaStream_t st);
+cudaError_t launch_group_measure(const GroupBatchArgs &g, int blocks, size_t smem, cudaStream_t st);
+size_t measure_smem_bytes_for(int L);
+
+// Block index of a group launch -> batch index (static indices only).
+__device__ __forceinline__ int group_member(const int (&off)[GROUP_MAX + 1], int n, int blk) {
+    int i = 0;
+#pragma unroll
+    for (int j = 1; j < GROUP_MAX; ++j)
+        if (j < n && blk >= off[j]) i = j;
+    return i;
+}
+
 // autocorr.cu
 cudaError_t launch_snapshot_reservoir(const Batch &b, int first, int count, uint32_t *snap, cudaStream_t st);
 cudaError_t launch_reservoir_overlap(const Batch &b, int first, int count, const uint32_t *snap,

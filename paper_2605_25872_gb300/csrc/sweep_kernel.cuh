@@ -240,13 +240,14 @@ struct SweepBounds {
         (RULE == PTHR_METROPOLIS && 65536 / (threads * 112) >= 2) ? 2 : 1;
 };
 
+// One block of the sweep launch: block `bid` of the launch described by a,
+// dynamic shared memory at smem.  Threads past the block's lattice lanes
+// (a launch shared with larger shapes) take part in the barriers only.
 template <int L, int RULE, int KT>
-__global__ void __launch_bounds__(SweepBounds<L, RULE>::threads, SweepBounds<L, RULE>::min_blocks)
-sweep_kernel(SweepArgs a) {
+__device__ __forceinline__ void sweep_block(const SweepArgs &a, int bid, unsigned char *smem) {
     using Gm = Geom<L>;
     constexpr int W = Gm::W, ROWS = Gm::ROWS, Lh = Gm::Lh, G = Gm::G;
     constexpr int LW = Gm::LAT_WORDS, LB = Gm::LAT_BYTES;
-    extern __shared__ __align__(16) unsigned char smem[];
     float *Js = reinterpret_cast<float *>(smem);                       // [3][LB]
     uint32_t *Ss = reinterpret_cast<uint32_t *>(smem + 12 * LB);       // [K][LW]
     __shared__ int s_lat[MAXK];
@@ -259,7 +260,7 @@ sweep_kernel(SweepArgs a) {
 
     const Batch &b = a.b;
     // ---- decode the task
-    int t = blockIdx.x;
+    int t = bid;
     const int nres_tasks = a.do_res ? a.res_tasks : 0;
     const int nall_res = a.sample_count * nres_tasks;
     int s, kind, chunk;
@@ -461,7 +462,7 @@ sweep_kernel(SweepArgs a) {
                                     q.wA >= 0 && q.wA < LW && q.wB >= 0 && q.wB < LW && q.yp >= 0 &&
                                     q.yp < LW && q.ym >= 0 && q.ym < LW && q.zp >= 0 && q.zp < LW &&
                                     q.zm >= 0 && q.zm < LW && 4 * q.own + 3 < LB && 4 * cm + 3 < LB &&
-                                    kbase + KT <= MAXK;
+                                    (kbase >= K || kbase + min(KT, K - kbase) <= MAXK);
                     if (!PTHR_DCHECK(b.status, in)) continue;
                 }
 #endif
@@ -779,6 +780,13 @@ sweep_kernel(SweepArgs a) {
         b.E[li] = exact_E ? (double)(long long)s_Ei[tid] * (-1.0 / 262144.0) : -s_E[tid];
         if (s_flips[tid]) atomicAdd(&b.flips[li], (unsigned long long)s_flips[tid]);
     }
+}
+
+template <int L, int RULE, int KT>
+__global__ void __launch_bounds__(SweepBounds<L, RULE>::threads, SweepBounds<L, RULE>::min_blocks)
+sweep_kernel(SweepArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    sweep_block<L, RULE, KT>(a, blockIdx.x, smem);
 }
 
 template <int L, int RULE, int KT>

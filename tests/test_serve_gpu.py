@@ -104,9 +104,68 @@ def test_group_graph_equals_separate_batches():
     for b in sep:
         b.emcs(5)
     g = Group(grp_b)
+    assert g.launches_per_emcs == 4          # one launch per EMCS step for all sizes
     g.emcs(5)
     g.synchronize()
     for a, b in zip(sep, grp_b):
         np.testing.assert_array_equal(a.export_spins().cpu().numpy(), b.export_spins().cpu().numpy())
         np.testing.assert_array_equal(a.obs.cpu().numpy(), b.obs.cpu().numpy())
         np.testing.assert_array_equal(a.energies.cpu().numpy(), b.energies.cpu().numpy())
+
+
+@pytest.mark.parametrize("rule", ["heatbath", "micsa"])
+def test_group_graph_equals_separate_batches_other_rules(rule):
+    from paper_2605_25872_gb300 import Group
+    cfgs = [BatchConfig(L=L, n_samples=2, n_temps=6, n_replicas=4, n_res=2, sweeps_per_emcs=2,
+                        res_sweeps_per_emcs=4, rule=rule) for L in (4, 10, 16)]
+    Js = [W.gaussian_couplings(c.L, 2, 80 + c.L) for c in cfgs]
+    seeds = [W.sample_seeds(90 + c.L, 2) for c in cfgs]
+    sep = [Batch(c, couplings=J, seeds=sd) for c, J, sd in zip(cfgs, Js, seeds)]
+    grp_b = [Batch(c, couplings=J, seeds=sd, stream=torch.cuda.Stream()) for c, J, sd in zip(cfgs, Js, seeds)]
+    for b in sep:
+        b.emcs(3)
+    g = Group(grp_b)
+    assert g.launches_per_emcs == 4
+    g.emcs(3)
+    g.synchronize()
+    for a, b in zip(sep, grp_b):
+        np.testing.assert_array_equal(a.export_spins().cpu().numpy(), b.export_spins().cpu().numpy())
+        np.testing.assert_array_equal(a.obs.cpu().numpy(), b.obs.cpu().numpy())
+
+
+def test_mixed_size_group_matches_the_oracle():
+    """One graph of four launches per EMCS over batches of L = 4, 6 and 8
+    (the EMCS of Sec. 3 for every sample whatever its size) against the FP64
+    oracle, sample by sample: every sample whose oracle run met no near tie
+    has the oracle's spins, permutations, energies and accumulators."""
+    import sys
+    sys.path.insert(0, __file__.rsplit("/", 1)[0])
+    from mirror import Mirror
+    from paper_2605_25872_gb300 import Group
+    cfgs = [BatchConfig(L=L, n_samples=3, n_temps=6, n_replicas=4, n_res=2, sweeps_per_emcs=2,
+                        res_sweeps_per_emcs=4) for L in (4, 6, 8)]
+    Js = [W.gaussian_couplings(c.L, 3, 120 + c.L) for c in cfgs]
+    seeds = [W.sample_seeds(W.SEED_BASE + 130 + c.L, 3) for c in cfgs]
+    batches = [Batch(c, couplings=J, seeds=sd, stream=torch.cuda.Stream()) for c, J, sd in zip(cfgs, Js, seeds)]
+    mirrors = [Mirror(c, J, sd) for c, J, sd in zip(cfgs, Js, seeds)]
+    g = Group(batches)
+    assert g.launches_per_emcs == 4
+    n_emcs = 4
+    g.emcs(n_emcs)
+    g.synchronize()
+    compared = 0
+    for b, m in zip(batches, mirrors):
+        tied = set()
+        for _ in range(n_emcs):
+            ties, pt_ties = m.emcs()
+            tied |= {s for s, _ in ties} | set(pt_ties)
+        spins = b.export_spins().cpu().numpy()
+        for s in range(b.cfg.n_samples):
+            if s in tied:
+                continue
+            np.testing.assert_array_equal(spins[s], m.spins()[s])
+            np.testing.assert_array_equal(b.perm.cpu().numpy()[s], m.perms()[s])
+            np.testing.assert_array_equal(b.energies.cpu().numpy()[s], m.energies()[s])
+            np.testing.assert_array_equal(b.obs.cpu().numpy()[s], m.samples[s].obs)
+            compared += 1
+    assert compared >= 7
