@@ -405,13 +405,15 @@ def run_gpu(args):
             _, cmean, cerr = spin_autocorrelation(sums, WL.n_replicas, WL.n_res, WL.V)
             autocorr = {"tau_sweeps": [WL.res_sweeps_per_emcs * (p + 1) for p in range(4)],
                         "C": [float(x) for x in cmean], "C_err": [float(x) for x in cerr],
-                        "samples": S, "clones_per_sample": WL.n_replicas * WL.n_res,
-                        "paper": "C(960) < 1e-3 (Sec. 3, ER)"}
-        serving = mixed = None
+                        "t_max": WL.t_max, "samples": S, "clones_per_sample": WL.n_replicas * WL.n_res,
+                        "paper": "C(960) < 1e-3 at the paper's T_max = 2 (Sec. 3, ER; App. A.2)"}
+            autocorr["t_max_2"] = autocorr_at(dev, 2.0)
+        serving = mixed = micsa = None
         if WL is W.WORKLOADS["c4"] and world == 1:
             serving = serve_measure(args.serve_budget, args.serve_requests, args.serve_mem_gb,
                                     args.serve_max_slots, args.serve_chunk)
             mixed = mixed_group_measure(dev)
+            micsa = micsa_measure(dev, J, seeds)
         result = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
@@ -432,6 +434,7 @@ def run_gpu(args):
             "serving": serving,
             "mixed_sizes": mixed,
             "reservoir_autocorrelation": autocorr,
+            "micsa": micsa,
             "cpu_baseline": cpu_baseline(),
             "e2e": e2e,
             "clocks": clocks,
@@ -555,6 +558,57 @@ def serve_measure(budget, n_req, mem_gb, max_slots, max_chunk):
                                    "4 reservoir clones, paper EMCS, couplings drawn on the device from each "
                                    "request's seed, 960-sweep reservoir pre-thermalisation at admission, "
                                    "Poisson arrivals at 0.8 x the measured capacity"}}
+
+
+def autocorr_at(dev, t_max, n_samples=256):
+    """C(tau) of the reservoir clones at T_max = t_max (the paper's L = 16
+    grid ends at T_max = 2, App. A.2) after the 960-sweep pre-thermalisation,
+    tau = 240 .. 960, same lattice size and reservoir as the workload."""
+    import dataclasses
+    import torch
+    from paper_2605_25872_gb300 import Batch
+    from paper_2605_25872_gb300.analysis import spin_autocorrelation
+    cfg = dataclasses.replace(batch_config(n_samples), t_max=t_max)
+    b = Batch(cfg, couplings=None, seeds=W.sample_seeds(W.batch_seed(WL.index) + 77777, n_samples), device=dev,
+              stream=torch.cuda.Stream(dev))
+    b.prethermalize(960)
+    sums = b.reservoir_autocorrelation(4, 240).cpu().numpy()
+    b.close()
+    _, cmean, cerr = spin_autocorrelation(sums, cfg.n_replicas, cfg.n_res, cfg.V)
+    return {"t_max": t_max, "tau_sweeps": [240, 480, 720, 960], "C": [float(x) for x in cmean],
+            "C_err": [float(x) for x in cerr], "samples": n_samples}
+
+
+def micsa_measure(dev, J, seeds, n_emcs=10):
+    """The same workload with the MicSA local update (App. A.1; the paper's
+    PTHR* for its late L=16 bins): EMCS and sweep-launch timing with CUDA
+    events (graph replay of whole EMCS)."""
+    import dataclasses
+    import torch
+    from paper_2605_25872_gb300 import Batch
+    cfg = dataclasses.replace(batch_config(len(seeds)), rule="micsa")
+    stream = torch.cuda.Stream(dev)
+    b = Batch(cfg, couplings=J, seeds=seeds, device=dev, stream=stream)
+    if WL.er_on and WL.res_pretherm_sweeps:
+        b.prethermalize(WL.res_pretherm_sweeps)
+    b.emcs(3, graph=True)
+    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        b.emcs(n_emcs, graph=True)
+        e1.record(stream)
+        b.sweep(WL.sweeps_per_emcs, WL.res_sweeps_per_emcs if WL.er_on else 0)
+        e2.record(stream)
+        b.houdayer()
+        b.swap(True, WL.er_on)
+        b.measure()
+    stream.synchronize()
+    pt, res = updates_per_emcs(len(seeds))
+    ms = e0.elapsed_time(e1) / n_emcs
+    ms_sweep = e1.elapsed_time(e2)
+    b.close()
+    return {"rule": "micsa", "updates_per_ns": (pt + res) / (ms * 1e6), "ms_per_emcs": ms,
+            "sweep_ms": ms_sweep, "sweep_updates_per_ns": (pt + res) / (ms_sweep * 1e6)}
 
 
 def mixed_group_measure(dev, slots=128, n_emcs=10):

@@ -160,6 +160,20 @@ int default_k(const pthr_config *c, int total_entries) {
     return (int)k;
 }
 
+// Streaming multiprocessors of the current device (queried once).
+int device_sms() {
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0, v = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0)
+            n = v;
+        else
+            return 152;
+    }
+    return n;
+}
+
 // forced_kt > 0: lattices per thread fixed (the mixed-L group sweep compiles
 // one value per lattice size); the lattices per block then follow from it.
 SweepShape sweep_shape(const pthr_batch *b, int forced_kt = 0) {
@@ -169,6 +183,13 @@ SweepShape sweep_shape(const pthr_batch *b, int forced_kt = 0) {
     const int nres = c->n_replicas * (c->n_res > 0 ? c->n_res : 1);
     sh.K_pt = b->tuning.pt_lattices_per_block > 0 ? b->tuning.pt_lattices_per_block : default_k(c, npt);
     sh.K_res = b->tuning.res_lattices_per_block > 0 ? b->tuning.res_lattices_per_block : default_k(c, nres);
+    if (b->tuning.res_lattices_per_block <= 0) {
+        // reservoir blocks run many sweeps each (240 per EMCS): with few
+        // samples, fewer lattices per block so that at least two such blocks
+        // per SM share the long tail
+        while (sh.K_res > 1 && (long)c->n_samples * ((nres + sh.K_res - 1) / sh.K_res) < 2L * device_sms())
+            sh.K_res = (sh.K_res + 1) / 2;
+    }
     if (sh.K_pt > npt) sh.K_pt = npt;
     if (sh.K_res > nres) sh.K_res = nres;
     const int G = sweep_groups_for(c->L);
