@@ -183,11 +183,12 @@ SweepShape sweep_shape(const pthr_batch *b, int forced_kt = 0) {
     const int nres = c->n_replicas * (c->n_res > 0 ? c->n_res : 1);
     sh.K_pt = b->tuning.pt_lattices_per_block > 0 ? b->tuning.pt_lattices_per_block : default_k(c, npt);
     sh.K_res = b->tuning.res_lattices_per_block > 0 ? b->tuning.res_lattices_per_block : default_k(c, nres);
-    if (b->tuning.res_lattices_per_block <= 0) {
-        // reservoir blocks run many sweeps each (240 per EMCS): with few
-        // samples, fewer lattices per block so that at least two such blocks
-        // per SM share the long tail
-        while (sh.K_res > 1 && (long)c->n_samples * ((nres + sh.K_res - 1) / sh.K_res) < 2L * device_sms())
+    if (b->tuning.res_lattices_per_block <= 0 && c->res_sweeps_per_emcs > 8 * c->sweeps_per_emcs) {
+        // reservoir blocks run many more sweeps than PT blocks (240 against
+        // 10 per EMCS): with fewer such blocks than SMs, halve their lattices
+        // once so that the long blocks cover every SM (splitting further
+        // costs more in per-block setup than the tail it saves)
+        if (sh.K_res > 4 && (long)c->n_samples * ((nres + sh.K_res - 1) / sh.K_res) < device_sms())
             sh.K_res = (sh.K_res + 1) / 2;
     }
     if (sh.K_pt > npt) sh.K_pt = npt;
@@ -247,6 +248,7 @@ pthr_status sweep_launch(pthr_batch *b, int n_pt, int n_res, int first, int coun
     a.sample_count = count;
     a.emcs_override = pretherm;
     a.Gt = sh.Gt;
+    a.shr8_mul = 1u << 24;
     out->a = a;
     out->blocks = count * ((a.do_res ? sh.res_tasks : 0) + (a.do_pt ? sh.pt_tasks : 0));
     out->threads = sh.threads;
