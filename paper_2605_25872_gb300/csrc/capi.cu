@@ -160,20 +160,6 @@ int default_k(const pthr_config *c, int total_entries) {
     return (int)k;
 }
 
-// Streaming multiprocessors of the current device (queried once).
-int device_sms() {
-    static int n = 0;
-    if (n == 0) {
-        int dev = 0, v = 0;
-        if (cudaGetDevice(&dev) == cudaSuccess &&
-            cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0)
-            n = v;
-        else
-            return 152;
-    }
-    return n;
-}
-
 // forced_kt > 0: lattices per thread fixed (the mixed-L group sweep compiles
 // one value per lattice size); the lattices per block then follow from it.
 SweepShape sweep_shape(const pthr_batch *b, int forced_kt = 0) {
@@ -183,14 +169,6 @@ SweepShape sweep_shape(const pthr_batch *b, int forced_kt = 0) {
     const int nres = c->n_replicas * (c->n_res > 0 ? c->n_res : 1);
     sh.K_pt = b->tuning.pt_lattices_per_block > 0 ? b->tuning.pt_lattices_per_block : default_k(c, npt);
     sh.K_res = b->tuning.res_lattices_per_block > 0 ? b->tuning.res_lattices_per_block : default_k(c, nres);
-    if (b->tuning.res_lattices_per_block <= 0 && c->res_sweeps_per_emcs > 8 * c->sweeps_per_emcs) {
-        // reservoir blocks run many more sweeps than PT blocks (240 against
-        // 10 per EMCS): with fewer such blocks than SMs, halve their lattices
-        // once so that the long blocks cover every SM (splitting further
-        // costs more in per-block setup than the tail it saves)
-        if (sh.K_res > 4 && (long)c->n_samples * ((nres + sh.K_res - 1) / sh.K_res) < device_sms())
-            sh.K_res = (sh.K_res + 1) / 2;
-    }
     if (sh.K_pt > npt) sh.K_pt = npt;
     if (sh.K_res > nres) sh.K_res = nres;
     const int G = sweep_groups_for(c->L);
@@ -248,7 +226,6 @@ pthr_status sweep_launch(pthr_batch *b, int n_pt, int n_res, int first, int coun
     a.sample_count = count;
     a.emcs_override = pretherm;
     a.Gt = sh.Gt;
-    a.shr8_mul = 1u << 24;
     out->a = a;
     out->blocks = count * ((a.do_res ? sh.res_tasks : 0) + (a.do_pt ? sh.pt_tasks : 0));
     out->threads = sh.threads;

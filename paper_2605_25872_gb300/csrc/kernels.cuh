@@ -17,8 +17,6 @@ struct SweepArgs {
     int emcs_override;                   // 1: counter word PRETHERM_EMCS, sweep index
                                          //    from the sample's PRETH counter
     int Gt;                              // groups per lattice lane (divides G and threads)
-    uint32_t shr8_mul;                   // 2^24: x >> 8 as the high word of x * 2^24 (an
-                                         // integer multiply, issued to the FMA pipe)
 };
 
 cudaError_t launch_sweep(const SweepArgs &a, int blocks, int threads, int KT, cudaStream_t st);

@@ -94,15 +94,6 @@ __device__ __forceinline__ u4 philox10_sweep(uint32_t ph, uint32_t pl, const Swe
     return u4{c0, c1, c2, c3};
 }
 
-// x >> 8 computed as the high word of x * m with m = 2^24 held in a
-// register: the multiply goes to the FMA pipe, which has room, instead of a
-// shift on the ALU pipe, which binds this kernel.
-__device__ __forceinline__ uint32_t shr8_on_fma(uint32_t x, uint32_t m) {
-    uint32_t r;
-    asm("mul.hi.u32 %0, %1, %2;" : "=r"(r) : "r"(x), "r"(m));
-    return r;
-}
-
 // Packed FP32 pairs (Blackwell f32x2 arithmetic): two independent IEEE
 // round-to-nearest operations per instruction.
 typedef unsigned long long f2;
@@ -626,8 +617,8 @@ __device__ __forceinline__ void sweep_block(const SweepArgs &a, int bid, unsigne
                             unpack2(mul2(tb2, tt), y0, y1);
                             const f2 negp = pack2(-fast_exp2(y0), -fast_exp2(y1));
                             // u - p < 0  <=>  accept (u = (x >> 8) 2^-24, exact)
-                            const f2 u2 = pack2(__uint2float_rz(shr8_on_fma(rw[2 * h], a.shr8_mul)),
-                                                __uint2float_rz(shr8_on_fma(rw[2 * h + 1], a.shr8_mul)));
+                            const f2 u2 = pack2(__uint2float_rz(rw[2 * h] >> 8),
+                                                __uint2float_rz(rw[2 * h + 1] >> 8));
                             unpack2(fma2(u2, sc2, negp), dv[2 * h], dv[2 * h + 1]);
                         }
                         // sign byte of each difference -> byte kk of the mask
