@@ -191,12 +191,16 @@ def sweep_roofline(n_sm, mhz, upd_per_s, measured):
     return roof
 
 
+RULE = "metropolis"        # local update rule of the timed batch (--rule; profiling cases)
+
+
 def batch_config(n_samples=None):
     from paper_2605_25872_gb300 import BatchConfig
     return BatchConfig(L=WL.L, n_samples=n_samples or WL.n_samples, n_temps=WL.n_temps,
                        t_min=WL.t_min, t_max=WL.t_max, n_replicas=WL.n_replicas,
                        n_res=WL.n_res if WL.er_on else 0, sweeps_per_emcs=WL.sweeps_per_emcs,
-                       res_sweeps_per_emcs=WL.res_sweeps_per_emcs, er_on=WL.er_on, cluster="acu")
+                       res_sweeps_per_emcs=WL.res_sweeps_per_emcs, er_on=WL.er_on, cluster="acu",
+                       rule=RULE)
 
 
 def updates_per_emcs(n_samples):
@@ -702,8 +706,14 @@ def main():
     ap.add_argument("--autotune", action="store_true", help="print the shape sweep for the workload")
     ap.add_argument("--workload", default="c4", choices=["c2", "c3", "c4"],
                     help="c4 (L=16 PTHR, the headline) or the batched L=8 / L=12 workloads")
+    ap.add_argument("--rule", default="metropolis", choices=["metropolis", "heatbath", "micsa"],
+                    help="local update rule of the timed batch (profiling cases; the headline is Metropolis)")
     args = ap.parse_args()
     WL = W.WORKLOADS[args.workload]
+    global RULE
+    RULE = args.rule
+    if RULE != "metropolis" and not args.no_extras:
+        ap.error("--rule other than metropolis is for --no-extras profiling runs")
     if args.workload != "c4":
         global METRIC
         METRIC = METRIC_OTHER.format(L=WL.L)

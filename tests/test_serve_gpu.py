@@ -169,3 +169,27 @@ def test_mixed_size_group_matches_the_oracle():
             np.testing.assert_array_equal(b.obs.cpu().numpy()[s], m.samples[s].obs)
             compared += 1
     assert compared >= 7
+
+
+def test_group_outside_the_compiled_sizes_falls_back_to_per_batch_graphs():
+    """A group with L = 18 (not compiled into the group kernels) and batches
+    of different update rules is captured as each batch's own EMCS on its
+    stream: same results as separate batches, more than four launches."""
+    from paper_2605_25872_gb300 import Group
+    cfgs = [BatchConfig(L=18, n_samples=1, n_temps=4, n_replicas=4, n_res=1, sweeps_per_emcs=1,
+                        res_sweeps_per_emcs=2),
+            BatchConfig(L=6, n_samples=2, n_temps=4, n_replicas=4, n_res=1, sweeps_per_emcs=1,
+                        res_sweeps_per_emcs=2, rule="heatbath")]
+    Js = [W.gaussian_couplings(c.L, c.n_samples, 160 + c.L) for c in cfgs]
+    seeds = [W.sample_seeds(170 + c.L, c.n_samples) for c in cfgs]
+    sep = [Batch(c, couplings=J, seeds=sd) for c, J, sd in zip(cfgs, Js, seeds)]
+    grp_b = [Batch(c, couplings=J, seeds=sd, stream=torch.cuda.Stream()) for c, J, sd in zip(cfgs, Js, seeds)]
+    for b in sep:
+        b.emcs(2)
+    g = Group(grp_b)
+    assert g.launches_per_emcs == 8
+    g.emcs(2)
+    g.synchronize()
+    for a, b in zip(sep, grp_b):
+        np.testing.assert_array_equal(a.export_spins().cpu().numpy(), b.export_spins().cpu().numpy())
+        np.testing.assert_array_equal(a.obs.cpu().numpy(), b.obs.cpu().numpy())
