@@ -317,6 +317,14 @@ def run_gpu(args):
     J = W.gaussian_couplings(WL.L, S, W.batch_seed(WL.index) + rank)
     stream = torch.cuda.Stream(dev)
     b = Batch(cfg, couplings=J, seeds=seeds, device=dev, stream=stream)
+    tuned_shape = None
+    if args.tuned:
+        # the autotuner's shape for this configuration (measured on this GPU
+        # on a scratch batch; shapes never change results)
+        from paper_2605_25872_gb300.autotune import autotune
+        tuned_shape = autotune(cfg, device=dev)
+        if tuned_shape:
+            b.set_tuning(**tuned_shape)
     if WL.er_on and WL.res_pretherm_sweeps:
         b.prethermalize(WL.res_pretherm_sweeps)
     pt_upd, res_upd = updates_per_emcs(S)
@@ -368,10 +376,25 @@ def run_gpu(args):
     assert b.poll(60000) == 0
 
     if args.no_extras:
+        # the same EMCS replayed from one captured CUDA graph
+        b.emcs(1, graph=True)
+        stream.synchronize()
+        gr0, gr1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            gr0.record(stream)
+            b.emcs(max(2, args.steps), graph=True)
+            gr1.record(stream)
+        stream.synchronize()
+        ms_gr = gr0.elapsed_time(gr1) / max(2, args.steps)
         if rank == 0:
             print(json.dumps({"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                              "updates_per_ns_graph": world * upd / (ms_gr * 1e6),
+                              "shape": tuned_shape or "default",
                               "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
-                              "samples": S, "phase_ms_sweep": ms_sweep, "clocks": clocks,
+                              "samples": S, "phase_ms_sweep": ms_sweep,
+                              "phase_ms": {n: float(phase[:, i].mean()) for i, n in
+                                           enumerate(("sweep", "houdayer", "swap", "measure"))},
+                              "clocks": clocks,
                               "note": "profiling case, not a headline line"}))
         if world > 1:
             dist.destroy_process_group()
@@ -593,6 +616,14 @@ def micsa_measure(dev, J, seeds, n_emcs=10):
     cfg = dataclasses.replace(batch_config(len(seeds)), rule="micsa")
     stream = torch.cuda.Stream(dev)
     b = Batch(cfg, couplings=J, seeds=seeds, device=dev, stream=stream)
+    tuned_shape = None
+    if args.tuned:
+        # the autotuner's shape for this configuration (measured on this GPU
+        # on a scratch batch; shapes never change results)
+        from paper_2605_25872_gb300.autotune import autotune
+        tuned_shape = autotune(cfg, device=dev)
+        if tuned_shape:
+            b.set_tuning(**tuned_shape)
     if WL.er_on and WL.res_pretherm_sweeps:
         b.prethermalize(WL.res_pretherm_sweeps)
     b.emcs(3, graph=True)
@@ -706,6 +737,8 @@ def main():
     ap.add_argument("--autotune", action="store_true", help="print the shape sweep for the workload")
     ap.add_argument("--workload", default="c4", choices=["c2", "c3", "c4"],
                     help="c4 (L=16 PTHR, the headline) or the batched L=8 / L=12 workloads")
+    ap.add_argument("--tuned", action="store_true",
+                    help="apply the autotuned kernel shape of the workload before timing")
     ap.add_argument("--rule", default="metropolis", choices=["metropolis", "heatbath", "micsa"],
                     help="local update rule of the timed batch (profiling cases; the headline is Metropolis)")
     args = ap.parse_args()

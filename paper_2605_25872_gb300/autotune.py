@@ -28,14 +28,28 @@ def _key(cfg: BatchConfig, device_name: str) -> str:
     return device_name + "|" + json.dumps(d, sort_keys=True)
 
 
+def sweep_lane_threads(L: int) -> list:
+    """Sweep block sizes below the default: whole lattice lanes of Gt threads
+    (Gt = the 4-site groups of one colour, or its largest divisor up to 512),
+    one, two or four lanes.  Fewer lanes give each thread more lattices, so
+    its couplings serve more updates, and give small batches more blocks."""
+    G = L * L * ((L // 2 + 3) // 4)
+    Gt = G if G <= 512 else max(d for d in range(1, 513) if G % d == 0)
+    return [Gt * p for p in (1, 2, 4) if p < 512 // Gt]
+
+
 def candidates(cfg: BatchConfig):
-    """Sweep shapes (PT / reservoir lattices per block), then cluster threads."""
+    """Sweep shapes (PT / reservoir lattices per block, sweep threads), then
+    cluster threads."""
     npt = cfg.n_replicas * cfg.n_temps
     nres = cfg.n_replicas * max(cfg.n_res, 1)
     ks = sorted({k for k in (4, 8, 12, 16, 24, 32, 48, 64) if k <= npt} | {npt if npt <= 64 else 64})
     kr = sorted({k for k in (2, 4, 8, 16, 32) if k <= nres} | {nres if nres <= 64 else 64})
-    for kp, krs in itertools.product(ks, kr):
-        yield {"pt_lattices_per_block": kp, "res_lattices_per_block": krs}
+    for kp, krs, th in itertools.product(ks, kr, [0] + sweep_lane_threads(cfg.L)):
+        shape = {"pt_lattices_per_block": kp, "res_lattices_per_block": krs}
+        if th:
+            shape["sweep_threads"] = th
+        yield shape
     V = cfg.L ** 3
     for ct in (64, 128, 256, 384, 512):
         if ct <= max(64, V // 2):
