@@ -192,6 +192,7 @@ def sweep_roofline(n_sm, mhz, upd_per_s, measured):
 
 
 RULE = "metropolis"        # local update rule of the timed batch (--rule; profiling cases)
+SPINS = "bytes"            # spin storage of the timed batches (--spin-layout)
 
 
 def batch_config(n_samples=None):
@@ -200,7 +201,7 @@ def batch_config(n_samples=None):
                        t_min=WL.t_min, t_max=WL.t_max, n_replicas=WL.n_replicas,
                        n_res=WL.n_res if WL.er_on else 0, sweeps_per_emcs=WL.sweeps_per_emcs,
                        res_sweeps_per_emcs=WL.res_sweeps_per_emcs, er_on=WL.er_on, cluster="acu",
-                       rule=RULE)
+                       rule=RULE, spin_layout=SPINS)
 
 
 def updates_per_emcs(n_samples):
@@ -276,14 +277,14 @@ def config_dict():
     emcs = (f"{WL.sweeps_per_emcs} sweep{'s' if WL.sweeps_per_emcs > 1 else ''} + ACU(T<1) + PT"
             + (f" + ER ({WL.res_sweeps_per_emcs} reservoir sweeps)" if WL.er_on else ""))
     lat = WL.n_samples * WL.lattices_per_sample
-    lat_bytes = 2 * WL.L * WL.L * ((WL.L // 2 + 3) // 4) * 4
+    lat_bytes = 2 * WL.L * WL.L * ((WL.L // 2 + 3) // 4) * 4 // (8 if SPINS == "bits" else 1)
     state_mb = (lat * lat_bytes + WL.n_samples * 3 * WL.V * 4) / 1e6
     return {"workload": f"{WL.name} (L={WL.L}, {WL.n_samples} samples x {WL.n_temps} T "
                         f"[{WL.t_min},{WL.t_max}] x {WL.n_replicas} replicas{res}; EMCS = {emcs})",
             "L": WL.L, "n_samples": WL.n_samples, "n_temps": WL.n_temps, "n_replicas": WL.n_replicas,
             "n_res": WL.n_res if WL.er_on else 0, "sweeps_per_emcs": WL.sweeps_per_emcs,
             "res_sweeps_per_emcs": WL.res_sweeps_per_emcs if WL.er_on else 0,
-            "update_rule": "metropolis", "couplings": "N(0,1) on the 2^-18 grid (seeded)",
+            "update_rule": RULE, "spin_layout": SPINS, "couplings": "N(0,1) on the 2^-18 grid (seeded)",
             "l2": (f"inputs larger than L2: {state_mb:.0f} MB of spins and couplings resident per GPU"
                    if state_mb > 129 else
                    f"{state_mb:.0f} MB of spins and couplings resident per GPU (fits in the 129 MB L2)")}
@@ -557,9 +558,9 @@ def serve_measure(budget, n_req, mem_gb, max_slots, max_chunk):
     mem = mem_gb * 1e9
     specs = []
     for L in W.SERVE_SIZES:
-        one = required_bytes(BatchConfig(L=L, n_samples=1, n_temps=24))
+        one = required_bytes(BatchConfig(L=L, n_samples=1, n_temps=24, spin_layout=SPINS))
         slots = int(min(max_slots, (mem / len(W.SERVE_SIZES)) // one))
-        specs.append(PoolSpec(L=L, slots=slots, n_temps=24))
+        specs.append(PoolSpec(L=L, slots=slots, n_temps=24, spin_layout=SPINS))
     # capacity probe: every pool full, EMCS timed with all pools in flight
     srv = Server(specs, max_chunk=max_chunk)
     probe = [Request(rid=-1 - i * 100000 - k, L=sp.L, seed=10 ** 6 + i * 100000 + k, budget_emcs=10 ** 6)
@@ -737,14 +738,17 @@ def main():
     ap.add_argument("--autotune", action="store_true", help="print the shape sweep for the workload")
     ap.add_argument("--workload", default="c4", choices=["c2", "c3", "c4"],
                     help="c4 (L=16 PTHR, the headline) or the batched L=8 / L=12 workloads")
+    ap.add_argument("--spin-layout", default="bytes", choices=["bytes", "bits"],
+                    help="spin storage in device memory (bits: 8x smaller; same results)")
     ap.add_argument("--tuned", action="store_true",
                     help="apply the autotuned kernel shape of the workload before timing")
     ap.add_argument("--rule", default="metropolis", choices=["metropolis", "heatbath", "micsa"],
                     help="local update rule of the timed batch (profiling cases; the headline is Metropolis)")
     args = ap.parse_args()
     WL = W.WORKLOADS[args.workload]
-    global RULE
+    global RULE, SPINS
     RULE = args.rule
+    SPINS = args.spin_layout
     if RULE != "metropolis" and not args.no_extras:
         ap.error("--rule other than metropolis is for --no-extras profiling runs")
     if args.workload != "c4":

@@ -78,13 +78,24 @@ typedef enum {
 enum { PTHR_METROPOLIS = 0, PTHR_HEATBATH = 1, PTHR_MICSA = 2 };
 enum { PTHR_CLUSTER_OFF = 0, PTHR_CLUSTER_ACU = 1, PTHR_CLUSTER_SINGLE = 2 };
 enum { PTHR_SWAP_PT = 1, PTHR_SWAP_ER = 2 };
+/* Spin storage in the workspace (the paper keeps spins as exact +-1; either
+ * form is exact).  BYTES: one byte per site slot, the form the kernels work
+ * on in shared memory.  BITS: one bit per site slot, 8x less device memory
+ * (more resident samples per GB); the sweep and cluster kernels expand a
+ * lattice to bytes when they stage it and pack it again on write-back.
+ * Results are identical in both layouts. */
+enum { PTHR_SPINS_BYTES = 0, PTHR_SPINS_BITS = 1 };
 enum { PTHR_OBS_MEASURE = 1, PTHR_OBS_READ_HOST = 2, PTHR_OBS_READ_DEVICE = 4, PTHR_OBS_RESET = 8,
        PTHR_OBS_CHAOS = 16 };
 
 /* Workspace sub-buffers (pthr_buffer_info).  Layouts:
  *  J      float    [S][3][V]        couplings, natural site order
  *  SPINS  uint8    [S][n_lat][lat_bytes] internal packed layout (use
- *                                   pthr_export_spins / pthr_import_spins)
+ *                                   pthr_export_spins / pthr_import_spins);
+ *                                   lat_bytes = pthr_lattice_storage_bytes(L,
+ *                                   spin_layout): one byte per site slot
+ *                                   (PTHR_SPINS_BYTES) or one bit
+ *                                   (PTHR_SPINS_BITS, 8x smaller)
  *  ENERGY double   [S][n_lat]       energy of every clone (Eq. (1)), FP64
  *  PERM   int32    [S][n_replicas][n_temps+n_res] position -> clone
  *  AGE    uint32   [S][n_replicas][max(n_res,1)] EMCS spent in the reservoir
@@ -134,7 +145,7 @@ typedef struct {
     int update_rule;          /* PTHR_METROPOLIS, PTHR_HEATBATH or PTHR_MICSA        */
     int cluster_mode;         /* PTHR_CLUSTER_OFF / _ACU / _SINGLE                   */
     int er_on;                /* 1: entropic reservoir step on                       */
-    int reserved;             /* must be 0                                           */
+    int spin_layout;          /* PTHR_SPINS_BYTES (0) or PTHR_SPINS_BITS             */
     double t_min, t_max;      /* temperature grid ends (t_max > t_min > 0)           */
     double acu_t_below;       /* cluster moves only at T_k < acu_t_below (paper: 1)  */
     uint64_t seed;            /* sample s uses Philox key seed + s unless seeds given */
@@ -160,8 +171,14 @@ PTHR_API pthr_status pthr_required_bytes(const pthr_config *cfg, size_t *bytes);
 PTHR_API pthr_status pthr_buffer_info(const pthr_config *cfg, int buffer, size_t *offset,
                                       size_t *bytes);
 
-/* Bytes of one lattice in the internal spin layout (for SPINS sizing). */
+/* Bytes of one lattice in the byte spin layout (PTHR_SPINS_BYTES), the
+ * form the kernels keep in shared memory. */
 PTHR_API pthr_status pthr_lattice_bytes(int L, size_t *bytes);
+
+/* Bytes of one lattice in the workspace for spin_layout (PTHR_SPINS_*):
+ * pthr_lattice_bytes(L) for bytes, an eighth of it for bits.  PTHR_E_INVAL
+ * for an invalid L or layout.  Host-only; no CUDA call. */
+PTHR_API pthr_status pthr_lattice_storage_bytes(int L, int spin_layout, size_t *bytes);
 
 /* Create a batch of cfg->n_samples samples in the caller-owned device
  * workspace (>= pthr_required_bytes bytes, 256-byte aligned).
@@ -316,7 +333,7 @@ PTHR_API pthr_status pthr_load(pthr_batch *b, const void *blob, size_t bytes);
  * n_res * V) for that sample.  The reservoir clones keep the extra sweeps
  * (a stationary evolution at T_max).  snapshot_device: caller-owned device
  * scratch, 16-byte aligned, at least count * n_replicas * n_res *
- * pthr_lattice_bytes(L) bytes (else PTHR_E_NOMEM); its contents are not
+ * pthr_lattice_storage_bytes(L, spin_layout) bytes (else PTHR_E_NOMEM); its contents are not
  * needed afterwards.  Needs n_res >= 1 and an EMCS boundary (PTHR_E_STATE).
  * Asynchronous. */
 PTHR_API pthr_status pthr_reservoir_autocorrelation(pthr_batch *b, int first, int count, int n_points,
@@ -333,8 +350,9 @@ PTHR_API pthr_status pthr_reservoir_autocorrelation(pthr_batch *b, int first, in
  * inside the library, which every GPU that loads the library keeps until
  * the process exits; it allocates nothing (no cudaMalloc or cudaFree, no
  * allocating library call).  The snapshot must fit in it: count *
- * n_replicas * n_res * pthr_lattice_bytes(L) <= 8 MiB (128 samples of the
- * L = 16, 4 x 4 reservoir), else PTHR_E_NOMEM and nothing runs; split
+ * n_replicas * n_res * pthr_lattice_storage_bytes(L, spin_layout) <= 8 MiB
+ * (128 samples of the L = 16, 4 x 4 reservoir in the byte layout, 1024 in
+ * the bit layout), else PTHR_E_NOMEM and nothing runs; split
  * larger batches into sample ranges.  The first call on a device looks up
  * the array's address on that device (the batch's device must be current,
  * else PTHR_E_INVAL); make that first call before any stream capture.

@@ -18,6 +18,7 @@ STATUS_NAMES = {0: "PTHR_OK", 1: "PTHR_E_INVAL", 2: "PTHR_E_NOMEM", 3: "PTHR_E_C
                 4: "PTHR_E_NOCONVERGE", 5: "PTHR_E_TIMEOUT", 6: "PTHR_E_STATE", 7: "PTHR_E_BOUNDS"}
 METROPOLIS, HEATBATH, MICSA = 0, 1, 2
 CLUSTER_OFF, CLUSTER_ACU, CLUSTER_SINGLE = 0, 1, 2
+SPINS_BYTES, SPINS_BITS = 0, 1
 SWAP_PT, SWAP_ER = 1, 2
 OBS_MEASURE, OBS_READ_HOST, OBS_READ_DEVICE, OBS_RESET, OBS_CHAOS = 1, 2, 4, 8, 16
 NOBS = 8
@@ -27,7 +28,8 @@ MAX_L = 24
  NBUF) = range(19)
 
 # every exported entry point of include/pthr.h
-EXPORTS = ("pthr_required_bytes", "pthr_buffer_info", "pthr_lattice_bytes", "pthr_create_batch",
+EXPORTS = ("pthr_required_bytes", "pthr_buffer_info", "pthr_lattice_bytes", "pthr_lattice_storage_bytes",
+           "pthr_create_batch",
            "pthr_destroy", "pthr_set_stream", "pthr_set_tuning", "pthr_get_tuning", "pthr_sweep",
            "pthr_houdayer", "pthr_cluster_labels", "pthr_swap", "pthr_observables", "pthr_emcs",
            "pthr_prethermalize_reservoir", "pthr_poll", "pthr_export_spins", "pthr_import_spins",
@@ -43,7 +45,7 @@ class Config(ctypes.Structure):
                 ("n_replicas", ctypes.c_int), ("n_res", ctypes.c_int),
                 ("sweeps_per_emcs", ctypes.c_int), ("res_sweeps_per_emcs", ctypes.c_int),
                 ("acu_interval", ctypes.c_int), ("update_rule", ctypes.c_int),
-                ("cluster_mode", ctypes.c_int), ("er_on", ctypes.c_int), ("reserved", ctypes.c_int),
+                ("cluster_mode", ctypes.c_int), ("er_on", ctypes.c_int), ("spin_layout", ctypes.c_int),
                 ("t_min", ctypes.c_double), ("t_max", ctypes.c_double),
                 ("acu_t_below", ctypes.c_double), ("seed", ctypes.c_uint64)]
 
@@ -81,6 +83,7 @@ def load(path: str | None = None):
         "pthr_required_bytes": [P(Config), P(sz)],
         "pthr_buffer_info": [P(Config), i, P(sz), P(sz)],
         "pthr_lattice_bytes": [i, P(sz)],
+        "pthr_lattice_storage_bytes": [i, i, P(sz)],
         "pthr_create_batch": [P(Config), vp, sz, vp, vp, vp, P(vp)],
         "pthr_set_stream": [vp, vp],
         "pthr_set_tuning": [vp, P(Tuning)],

@@ -178,3 +178,32 @@ def autotune_schedule(cfg: BatchConfig, intervals=(1, 2, 4, 8), max_cluster_shar
             chosen = row["acu_interval"]
             break
     return chosen, table
+
+
+def autotune_spin_layout(cfg: BatchConfig, emcs: int = 4, warm_emcs: int = 4, device="cuda",
+                         memory_weight: float = 0.0):
+    """Spin storage for cfg: times whole EMCS with the spins stored as bytes
+    and as bits (same couplings and seeds, so the same trajectory) and returns
+    (layout, table).  The layout is fixed when a batch is created, so this is
+    a recommendation for BatchConfig.spin_layout.  With memory_weight > 0 the
+    bit layout wins unless it is slower by more than that fraction (its
+    workspace holds 8x fewer spin bytes: more resident samples per GB)."""
+    import torch
+    rng = np.random.default_rng(2)
+    J = (np.rint(rng.standard_normal((cfg.n_samples, 3, cfg.L ** 3)) * 2 ** 18) / 2 ** 18).astype(np.float32)
+    table = {}
+    for layout in ("bytes", "bits"):
+        c = BatchConfig(**{**cfg.__dict__, "spin_layout": layout})
+        st = torch.cuda.Stream(device)
+        b = Batch(c, couplings=J, device=device, stream=st)
+        b.emcs(warm_emcs)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(st):
+            e0.record(st)
+            b.emcs(emcs)
+            e1.record(st)
+        st.synchronize()
+        table[layout] = {"ms_per_emcs": e0.elapsed_time(e1) / emcs, "workspace_bytes": b.nbytes}
+        b.close()
+    fast = table["bits"]["ms_per_emcs"] <= table["bytes"]["ms_per_emcs"] * (1.0 + memory_weight)
+    return ("bits" if fast else "bytes"), table

@@ -18,6 +18,8 @@ from ._lib import check
 RULES = {"metropolis": _lib.METROPOLIS, "heatbath": _lib.HEATBATH, "micsa": _lib.MICSA}
 LIVE = weakref.WeakSet()      # open batches (the tests check their guard blocks)
 CLUSTERS = {"off": _lib.CLUSTER_OFF, "acu": _lib.CLUSTER_ACU, "single": _lib.CLUSTER_SINGLE}
+# spin storage in the workspace: one byte or one bit per site slot
+SPIN_LAYOUTS = {"bytes": _lib.SPINS_BYTES, "bits": _lib.SPINS_BITS}
 
 
 @dataclass
@@ -37,11 +39,13 @@ class BatchConfig:
     er_on: bool = True
     acu_t_below: float = 1.0
     seed: int = 0
+    spin_layout: str = "bytes"
 
     def to_c(self) -> _lib.Config:
         return _lib.Config(self.L, self.n_samples, self.n_temps, self.n_replicas, self.n_res,
                            self.sweeps_per_emcs, self.res_sweeps_per_emcs, self.acu_interval,
-                           RULES[self.rule], CLUSTERS[self.cluster], int(self.er_on), 0,
+                           RULES[self.rule], CLUSTERS[self.cluster], int(self.er_on),
+                           SPIN_LAYOUTS[self.spin_layout],
                            float(self.t_min), float(self.t_max), float(self.acu_t_below),
                            int(self.seed) & 0xFFFFFFFFFFFFFFFF)
 
@@ -104,6 +108,10 @@ class Batch:
             assert seeds.size == cfg.n_samples
         self._cc = cfg.to_c()
         h = ctypes.c_void_p()
+        # the workspace and any device couplings come from torch's current
+        # stream; the library works on self.stream
+        self.stream.wait_stream(torch.cuda.current_stream(self.device))
+        self.ws.record_stream(self.stream)
         with torch.cuda.device(self.device):
             check(self.lib.pthr_create_batch(ctypes.byref(self._cc), ctypes.c_void_p(self.ws.data_ptr()),
                                              self.nbytes, _ptr(couplings), _ptr(seeds),
@@ -227,25 +235,37 @@ class Batch:
     def poll(self, timeout_ms: int = -1) -> int:
         return self.lib.pthr_poll(self.h, timeout_ms)
 
+    def _enqueue_with(self, out: torch.Tensor, call):
+        """Run `call` on the batch's stream after the work queued so far on
+        torch's current stream (which made `out`), and order later work on
+        the current stream after it."""
+        cur = torch.cuda.current_stream(self.device)
+        self.stream.wait_stream(cur)
+        call()
+        out.record_stream(self.stream)
+        cur.wait_stream(self.stream)
+        return out
+
     def export_spins(self) -> torch.Tensor:
         c = self.cfg
         out = torch.empty((c.n_samples, c.n_lat, c.V), dtype=torch.int8, device=self.device)
-        check(self.lib.pthr_export_spins(self.h, ctypes.c_void_p(out.data_ptr())), self.h)
-        return out
+        return self._enqueue_with(out, lambda: check(
+            self.lib.pthr_export_spins(self.h, ctypes.c_void_p(out.data_ptr())), self.h))
 
     def import_spins(self, spins: torch.Tensor):
         c = self.cfg
         spins = spins.to(device=self.device, dtype=torch.int8).contiguous()
         assert spins.numel() == c.n_samples * c.n_lat * c.V
-        check(self.lib.pthr_import_spins(self.h, ctypes.c_void_p(spins.data_ptr())), self.h)
+        self._enqueue_with(spins, lambda: check(
+            self.lib.pthr_import_spins(self.h, ctypes.c_void_p(spins.data_ptr())), self.h))
         self.stream.synchronize()
 
     def cluster_labels(self) -> torch.Tensor:
         c = self.cfg
         out = torch.full((c.n_samples, c.n_replicas // 2, c.n_temps, c.V), -1, dtype=torch.int32,
                          device=self.device)
-        check(self.lib.pthr_cluster_labels(self.h, ctypes.c_void_p(out.data_ptr())), self.h)
-        return out
+        return self._enqueue_with(out, lambda: check(
+            self.lib.pthr_cluster_labels(self.h, ctypes.c_void_p(out.data_ptr())), self.h))
 
     def reset_samples(self, first: int, count: int, seeds, couplings=None, pretherm_sweeps: int = 0):
         seeds = np.ascontiguousarray(np.asarray(seeds, dtype=np.uint64))
@@ -296,8 +316,10 @@ class Batch:
         return out
 
     def lattice_bytes(self) -> int:
+        """Workspace bytes of one lattice in this batch's spin layout."""
         n = ctypes.c_size_t(0)
-        check(self.lib.pthr_lattice_bytes(self.cfg.L, ctypes.byref(n)))
+        check(self.lib.pthr_lattice_storage_bytes(self.cfg.L, SPIN_LAYOUTS[self.cfg.spin_layout],
+                                                  ctypes.byref(n)))
         return n.value
 
     def check_canaries(self) -> int:
@@ -347,36 +369,6 @@ class Group:
         n = ctypes.c_int(0)
         check(self.lib.pthr_group_info(self.h, ctypes.byref(n)))
         return n.value
-
-    def reservoir_autocorrelation(self, n_points: int, sweeps_per_point: int, first: int = 0,
-                                  count: int | None = None) -> torch.Tensor:
-        """Integer sums of s_i(t) s_i(t + tau) over every reservoir clone and
-        site of each sample, tau = sweeps_per_point, 2 sweeps_per_point, ...
-        (pthr_reservoir_autocorrelation); device int64 [count, n_points]."""
-        c = self.cfg
-        count = c.n_samples - first if count is None else count
-        nbytes = count * c.n_replicas * c.n_res * self.lattice_bytes()
-        snap = torch.empty(max(nbytes, 16), dtype=torch.uint8, device=self.device)
-        out = torch.zeros((count, n_points), dtype=torch.int64, device=self.device)
-        check(self.lib.pthr_reservoir_autocorrelation(self.h, first, count, n_points, sweeps_per_point,
-                                                      ctypes.c_void_p(snap.data_ptr()), snap.numel(),
-                                                      ctypes.c_void_p(out.data_ptr())), self.h)
-        self.stream.synchronize()
-        return out
-
-    def lattice_bytes(self) -> int:
-        n = ctypes.c_size_t(0)
-        check(self.lib.pthr_lattice_bytes(self.cfg.L, ctypes.byref(n)))
-        return n.value
-
-    def check_canaries(self) -> int:
-        """-1 if every guard block after a workspace sub-buffer is intact,
-        else the PTHR_BUF_* index of the first overwritten one."""
-        bad = ctypes.c_int(-1)
-        st = self.lib.pthr_check_canaries(self.h, ctypes.byref(bad))
-        if st not in (_lib.PTHR_OK, _lib.PTHR_E_BOUNDS):
-            check(st, self.h)
-        return bad.value
 
     def synchronize(self):
         self.stream.synchronize()

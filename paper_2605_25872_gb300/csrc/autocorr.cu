@@ -53,11 +53,15 @@ __global__ void overlap_kernel(Batch b, int first, int count, const uint32_t *sn
         if (!PTHR_DCHECK(b.status, clone >= 0 && clone < b.NSLOT)) clone = b.NT + r;
         const uint32_t *cur = b.spins + ((size_t)s * b.NLAT + g * b.NSLOT + clone) * b.lat_words;
         const uint32_t *old = snap + ((size_t)(s - first) * nres + e) * b.lat_words;
-        for (int w = threadIdx.x; w < b.lat_words; w += blockDim.x) {
-            const int j = w % W;
-            const int nv = Lh - 4 * j;   // real sites in this word (the rest is row padding)
-            const uint32_t vm = nv >= 4 ? 0x80808080u : (0x80808080u >> (8 * (4 - nv)));
-            ndiff += __popc((cur[w] ^ old[w]) & vm);
+        if (b.bits) {                    // one bit per slot; row padding is always 0
+            for (int w = threadIdx.x; w < b.lat_words; w += blockDim.x) ndiff += __popc(cur[w] ^ old[w]);
+        } else {
+            for (int w = threadIdx.x; w < b.lat_words; w += blockDim.x) {
+                const int j = w % W;
+                const int nv = Lh - 4 * j;   // real sites in this word (the rest is row padding)
+                const uint32_t vm = nv >= 4 ? 0x80808080u : (0x80808080u >> (8 * (4 - nv)));
+                ndiff += __popc((cur[w] ^ old[w]) & vm);
+            }
         }
     }
     __shared__ int s_sum[32];

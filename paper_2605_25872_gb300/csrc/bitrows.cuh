@@ -26,12 +26,6 @@ __device__ __forceinline__ uint32_t compact_bits(uint32_t v) {
     return v;
 }
 
-// bit 7 of the four bytes of w (the sign of a packed spin, or where two
-// packed words differ) as the low four bits; a multiply gathers them
-__device__ __forceinline__ uint32_t sign_nibble(uint32_t w) {
-    return ((w & 0x80808080u) * 0x00204081u) >> 28;
-}
-
 // L-bit row rotated so that bit x holds bit (x + 1) mod L
 template <int L>
 __device__ __forceinline__ uint32_t rot_next(uint32_t v) {
@@ -39,8 +33,9 @@ __device__ __forceinline__ uint32_t rot_next(uint32_t v) {
 }
 
 // Row r = y + L z of the bit mask where lattices A and B differ (q_i = -1):
-// bit x set iff the spins at x + L r differ.
-template <int L>
+// bit x set iff the spins at x + L r differ.  A and B in the storage layout
+// (BITS: the bit layout, else the byte layout).
+template <int L, bool BITS = false>
 __device__ __forceinline__ uint32_t diff_row(const uint32_t *A, const uint32_t *B, int r) {
     using Gm = Geom<L>;
     constexpr int W = Gm::W, ROWS = Gm::ROWS, Lh = Gm::Lh;
@@ -51,7 +46,10 @@ __device__ __forceinline__ uint32_t diff_row(const uint32_t *A, const uint32_t *
 #pragma unroll
         for (int j = 0; j < W; ++j) {
             const int w = (c * ROWS + r) * W + j;
-            acc |= sign_nibble(A[w] ^ B[w]) << (4 * j);
+            if (BITS)
+                acc |= (((A[w >> 3] ^ B[w >> 3]) >> (4 * (w & 7))) & 0xFu) << (4 * j);
+            else
+                acc |= sign_nibble(A[w] ^ B[w]) << (4 * j);
         }
         bits[c] = acc & ((1u << Lh) - 1u);
     }

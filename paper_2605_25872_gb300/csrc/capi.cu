@@ -92,7 +92,8 @@ pthr_status check_config(const pthr_config *c) {
         return fail(nullptr, PTHR_E_INVAL, "cluster moves need an even n_replicas >= 2");
     if (!(c->t_min > 0.0) || !(c->t_max > c->t_min))
         return fail(nullptr, PTHR_E_INVAL, "need 0 < t_min < t_max");
-    if (c->reserved != 0) return fail(nullptr, PTHR_E_INVAL, "reserved must be 0");
+    if (c->spin_layout != PTHR_SPINS_BYTES && c->spin_layout != PTHR_SPINS_BITS)
+        return fail(nullptr, PTHR_E_INVAL, "unknown spin_layout %d", c->spin_layout);
     return PTHR_OK;
 }
 
@@ -116,7 +117,7 @@ Layout make_layout(const pthr_config *c) {
     const size_t NP = (size_t)(n_pairs(c) > 0 ? n_pairs(c) : 1);
     Layout l{};
     l.len[PTHR_BUF_J] = S * 3 * V * sizeof(float);
-    l.len[PTHR_BUF_SPINS] = S * NL * (size_t)lattice_words(c->L) * 4;
+    l.len[PTHR_BUF_SPINS] = S * NL * (size_t)storage_words(c->L, c->spin_layout) * 4;
     l.len[PTHR_BUF_ENERGY] = S * NL * sizeof(double);
     l.len[PTHR_BUF_PERM] = S * NR * (size_t)n_slot(c) * sizeof(int32_t);
     l.len[PTHR_BUF_AGE] = S * NR * NRES * sizeof(uint32_t);
@@ -339,6 +340,14 @@ PTHR_API pthr_status pthr_lattice_bytes(int L, size_t *bytes) {
     return PTHR_OK;
 }
 
+PTHR_API pthr_status pthr_lattice_storage_bytes(int L, int spin_layout, size_t *bytes) {
+    if (L < 2 || L > PTHR_MAX_L || (L & 1) || !bytes) return fail(nullptr, PTHR_E_INVAL, "bad L");
+    if (spin_layout != PTHR_SPINS_BYTES && spin_layout != PTHR_SPINS_BITS)
+        return fail(nullptr, PTHR_E_INVAL, "unknown spin_layout %d", spin_layout);
+    *bytes = (size_t)storage_words(L, spin_layout) * 4;
+    return PTHR_OK;
+}
+
 PTHR_API pthr_status pthr_create_batch(const pthr_config *cfg, void *device_workspace, size_t workspace_bytes,
                                        const float *couplings, const uint64_t *seeds, void *stream,
                                        pthr_batch **out) {
@@ -391,7 +400,8 @@ PTHR_API pthr_status pthr_create_batch(const pthr_config *cfg, void *device_work
     d.NSLOT = n_slot(cfg);
     d.NLAT = n_lat(cfg);
     d.NPAIR = n_pairs(cfg);
-    d.lat_words = lattice_words(cfg->L);
+    d.lat_words = storage_words(cfg->L, cfg->spin_layout);
+    d.bits = cfg->spin_layout == PTHR_SPINS_BITS ? 1 : 0;
     d.rule = cfg->update_rule;
     d.cluster_mode = cfg->cluster_mode;
     d.acu_interval = cfg->acu_interval;
@@ -911,7 +921,7 @@ PTHR_API pthr_status pthr_reservoir_autocorrelation(pthr_batch *b, int first, in
         (long long)n_points * sweeps_per_point >= (1LL << 23) || !snapshot_device || !out_device)
         return fail(b, PTHR_E_INVAL, "bad sample range, point count, sweeps or NULL buffer");
     if (((uintptr_t)snapshot_device) & 15) return fail(b, PTHR_E_INVAL, "snapshot must be 16-byte aligned");
-    const size_t need = (size_t)count * b->cfg.n_replicas * b->cfg.n_res * (size_t)lattice_words(b->cfg.L) * 4;
+    const size_t need = (size_t)count * b->cfg.n_replicas * b->cfg.n_res * (size_t)b->dev.lat_words * 4;
     if (snapshot_bytes < need)
         return fail(b, PTHR_E_NOMEM, "snapshot needs %zu bytes, got %zu", need, snapshot_bytes);
     if (b->pt_sweep_off || b->res_sweep_off)
@@ -934,7 +944,7 @@ PTHR_API pthr_status pthr_reservoir_autocorrelation_noalloc(pthr_batch *b, int f
     if (first < 0 || count < 1 || first + count > b->cfg.n_samples || n_points < 1 || sweeps_per_point < 1 ||
         !out_device)
         return fail(b, PTHR_E_INVAL, "bad sample range, point count, sweeps or NULL output");
-    const size_t need = (size_t)count * b->cfg.n_replicas * b->cfg.n_res * (size_t)lattice_words(b->cfg.L) * 4;
+    const size_t need = (size_t)count * b->cfg.n_replicas * b->cfg.n_res * (size_t)b->dev.lat_words * 4;
     cudaPointerAttributes pa{};
     int dev = 0;
     CUDA_TRY(b, cudaPointerGetAttributes(&pa, b->ws), "workspace attributes");

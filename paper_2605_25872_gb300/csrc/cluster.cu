@@ -54,7 +54,7 @@ __device__ __forceinline__ void unite(volatile int *parent, int a, int b, int ca
     ok = false;
 }
 
-// compact_bits, spread_bits, sign_nibble and rot_next: geometry.cuh
+// compact_bits, spread_bits and rot_next: bitrows.cuh; sign_nibble: pthr_internal.cuh
 
 // natural site index of byte kk of packed word w
 template <int L>
@@ -155,15 +155,27 @@ __device__ __forceinline__ void cluster_block(const ClusterArgs &a, int bid, uns
     if (!PTHR_DCHECK(b.status, la >= ga * b.NSLOT && la < (ga + 1) * b.NSLOT &&
                                 lb >= gb * b.NSLOT && lb < (gb + 1) * b.NSLOT && gb < b.NR)) return;
     const uint32_t pair_id = (uint32_t)(P * b.NT + k);
-    uint32_t *ga_ptr = b.spins + ((size_t)s * b.NLAT + la) * LW;
-    uint32_t *gb_ptr = b.spins + ((size_t)s * b.NLAT + lb) * LW;
+    uint32_t *ga_ptr = b.spins + ((size_t)s * b.NLAT + la) * b.lat_words;
+    uint32_t *gb_ptr = b.spins + ((size_t)s * b.NLAT + lb) * b.lat_words;
+    constexpr int LB8 = LW / 8;     // bit words per lattice (bit storage)
 
     if (tid == 0) { s_ok = 1; s_nneg = 0; s_root = -1; s_nclus = 0; s_nflip = 0; }
     if (tid < 2) s_E[tid] = 0.0;
     if (tid == 0) s_Ei[0] = 0ull;
-    for (int i = tid; i < LW / 4; i += T) {
-        reinterpret_cast<uint4 *>(sa)[i] = reinterpret_cast<const uint4 *>(ga_ptr)[i];
-        reinterpret_cast<uint4 *>(sb)[i] = reinterpret_cast<const uint4 *>(gb_ptr)[i];
+    if (b.bits) {
+        for (int i = tid; i < 2 * LB8; i += T) {
+            const int u = i < LB8 ? i : i - LB8;
+            uint4 lo, hi;
+            expand_bits(i < LB8 ? ga_ptr[u] : gb_ptr[u], lo, hi);
+            uint4 *d = reinterpret_cast<uint4 *>((i < LB8 ? sa : sb) + 8 * u);
+            d[0] = lo;
+            d[1] = hi;
+        }
+    } else {
+        for (int i = tid; i < LW / 4; i += T) {
+            reinterpret_cast<uint4 *>(sa)[i] = reinterpret_cast<const uint4 *>(ga_ptr)[i];
+            reinterpret_cast<uint4 *>(sb)[i] = reinterpret_cast<const uint4 *>(gb_ptr)[i];
+        }
     }
     __syncthreads();
     // q bits of every natural x row r = y + L z: bit x of qrow[r] is 1 iff
@@ -391,9 +403,17 @@ __device__ __forceinline__ void cluster_block(const ClusterArgs &a, int bid, uns
         if ((tid & 31) == 0) { atomicAdd(&s_E[0], ea); atomicAdd(&s_E[1], eb); }
     }
     __syncthreads();
-    for (int i = tid; i < LW / 4; i += T) {
-        reinterpret_cast<uint4 *>(ga_ptr)[i] = reinterpret_cast<const uint4 *>(sa)[i];
-        reinterpret_cast<uint4 *>(gb_ptr)[i] = reinterpret_cast<const uint4 *>(sb)[i];
+    if (b.bits) {
+        for (int i = tid; i < 2 * LB8; i += T) {
+            const int u = i < LB8 ? i : i - LB8;
+            const uint4 *w = reinterpret_cast<const uint4 *>((i < LB8 ? sa : sb) + 8 * u);
+            (i < LB8 ? ga_ptr : gb_ptr)[u] = pack_bits(w[0], w[1]);
+        }
+    } else {
+        for (int i = tid; i < LW / 4; i += T) {
+            reinterpret_cast<uint4 *>(ga_ptr)[i] = reinterpret_cast<const uint4 *>(sa)[i];
+            reinterpret_cast<uint4 *>(gb_ptr)[i] = reinterpret_cast<const uint4 *>(sb)[i];
+        }
     }
     if (tid == 0) {
         double *E = b.E + (size_t)s * b.NLAT;

@@ -107,7 +107,7 @@ template <int L>
 __device__ __forceinline__ void measure_block(const Batch &b, int first, int count, int chaos, int bid,
                                               unsigned char *smem) {
     using Gm = Geom<L>;
-    constexpr int V = Gm::V, LW = Gm::LAT_WORDS, ROWS = Gm::ROWS;
+    constexpr int V = Gm::V, ROWS = Gm::ROWS;
     uint32_t *s_q = reinterpret_cast<uint32_t *>(smem);   // [MEASURE_WARPS][ROWS]
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int item = bid * MEASURE_WARPS + wid;
@@ -116,7 +116,8 @@ __device__ __forceinline__ void measure_block(const Batch &b, int first, int cou
     if (!PTHR_DCHECK(b.status, s >= 0 && s < b.S)) return;
     if (!b.active[s]) return;
     const int32_t *perm = b.perm + (size_t)s * b.NR * b.NSLOT;
-    const uint32_t *spins = b.spins + (size_t)s * b.NLAT * LW;
+    const int lw = b.lat_words;                       // storage words per lattice
+    const uint32_t *spins = b.spins + (size_t)s * b.NLAT * lw;
     uint32_t *qr = s_q + wid * ROWS;
     int tn = 0, td = 0, tc = 0;                       // pair `lane`'s counts
     for (int P = 0; P < b.NPAIR; ++P) {
@@ -124,10 +125,10 @@ __device__ __forceinline__ void measure_block(const Batch &b, int first, int cou
         const int lb = (2 * P + 1) * b.NSLOT + perm[(2 * P + 1) * b.NSLOT + k];
         if (!PTHR_DCHECK(b.status, la >= 2 * P * b.NSLOT && la < (2 * P + 1) * b.NSLOT &&
                                     lb >= (2 * P + 1) * b.NSLOT && lb < (2 * P + 2) * b.NSLOT)) return;
-        const uint32_t *A = spins + (size_t)la * LW, *B = spins + (size_t)lb * LW;
+        const uint32_t *A = spins + (size_t)la * lw, *B = spins + (size_t)lb * lw;
         int nneg = 0, ndiff = 0, cneg = 0;
         for (int r = lane; r < ROWS; r += 32) {
-            const uint32_t q = diff_row<L>(A, B, r);
+            const uint32_t q = b.bits ? diff_row<L, true>(A, B, r) : diff_row<L>(A, B, r);
             qr[r] = q;
             nneg += __popc(q);
         }
@@ -140,8 +141,9 @@ __device__ __forceinline__ void measure_block(const Batch &b, int first, int cou
         }
         if (chaos) {
             // temperature chaos: clone of group 2P at T_0 against group 2P+1 at T_k
-            const uint32_t *A0 = spins + (size_t)(2 * P * b.NSLOT + perm[2 * P * b.NSLOT]) * LW;
-            for (int r = lane; r < ROWS; r += 32) cneg += __popc(diff_row<L>(A0, B, r));
+            const uint32_t *A0 = spins + (size_t)(2 * P * b.NSLOT + perm[2 * P * b.NSLOT]) * lw;
+            for (int r = lane; r < ROWS; r += 32)
+                cneg += __popc(b.bits ? diff_row<L, true>(A0, B, r) : diff_row<L>(A0, B, r));
         }
         __syncwarp();                                 // qr is reused by the next pair
         nneg = __reduce_add_sync(0xffffffffu, nneg);

@@ -58,14 +58,18 @@ __global__ void init_spins_kernel(Batch b, int first, int count) {
     const unsigned long long seed = b.seeds[s];
     const u4 w = philox10((uint32_t)q, (uint32_t)lat, 0u, TAG_INIT, (uint32_t)seed, (uint32_t)(seed >> 32));
     const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
-    unsigned char *S = reinterpret_cast<unsigned char *>(b.spins + ((size_t)s * b.NLAT + lat) * b.lat_words);
+    uint32_t *Sw = b.spins + ((size_t)s * b.NLAT + lat) * b.lat_words;
+    unsigned char *S = reinterpret_cast<unsigned char *>(Sw);
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         const int i = 4 * q + k;
         if (i >= V) break;
         int word, byte;
         slot_rt(b.L, i, word, byte);
-        S[4 * word + byte] = (ws[k] >> 31) ? SPIN_DN : SPIN_UP;
+        if (!b.bits)
+            S[4 * word + byte] = (ws[k] >> 31) ? SPIN_DN : SPIN_UP;
+        else if (ws[k] >> 31)   // bit storage, cleared before: set the -1 spins
+            atomicOr(&Sw[(4 * word + byte) >> 5], 1u << ((4 * word + byte) & 31));
     }
 }
 
@@ -114,8 +118,10 @@ __global__ void export_kernel(Batch b, int8_t *out) {
         const int i = (int)(idx % V);
         int word, byte;
         slot_rt(b.L, i, word, byte);
-        const unsigned char *S = reinterpret_cast<const unsigned char *>(b.spins + lat * b.lat_words);
-        out[idx] = (S[4 * word + byte] == SPIN_DN) ? (int8_t)-1 : (int8_t)1;
+        const uint32_t *Sw = b.spins + lat * b.lat_words;
+        const bool down = b.bits ? ((Sw[(4 * word + byte) >> 5] >> ((4 * word + byte) & 31)) & 1u) != 0u
+                                 : reinterpret_cast<const unsigned char *>(Sw)[4 * word + byte] == SPIN_DN;
+        out[idx] = down ? (int8_t)-1 : (int8_t)1;
     }
 }
 
@@ -128,8 +134,14 @@ __global__ void import_kernel(Batch b, const int8_t *in) {
         const int i = (int)(idx % V);
         int word, byte;
         slot_rt(b.L, i, word, byte);
-        unsigned char *S = reinterpret_cast<unsigned char *>(b.spins + lat * b.lat_words);
-        S[4 * word + byte] = (in[idx] < 0) ? SPIN_DN : SPIN_UP;
+        uint32_t *Sw = b.spins + lat * b.lat_words;
+        if (b.bits) {   // other threads set other bits of the same word
+            const uint32_t m = 1u << ((4 * word + byte) & 31);
+            if (in[idx] < 0) atomicOr(&Sw[(4 * word + byte) >> 5], m);
+            else atomicAnd(&Sw[(4 * word + byte) >> 5], ~m);
+        } else {
+            reinterpret_cast<unsigned char *>(Sw)[4 * word + byte] = (in[idx] < 0) ? SPIN_DN : SPIN_UP;
+        }
     }
 }
 
@@ -149,8 +161,9 @@ cudaError_t launch_couplings_from_seed(const Batch &b, int first, int count, cud
 
 cudaError_t launch_init_state(const Batch &b, int first, int count, cudaStream_t st) {
     const size_t lat_bytes = (size_t)b.lat_words * 4;
+    // every slot +1 first (row padding included): 0x3F bytes, or clear bits
     cudaError_t e = cudaMemsetAsync(reinterpret_cast<unsigned char *>(b.spins) + (size_t)first * b.NLAT * lat_bytes,
-                                    SPIN_UP, (size_t)count * b.NLAT * lat_bytes, st);
+                                    b.bits ? 0 : SPIN_UP, (size_t)count * b.NLAT * lat_bytes, st);
     if (e != cudaSuccess) return e;
     const int V = b.L * b.L * b.L;
     const long long n = (long long)count * b.NLAT * ((V + 3) / 4);

@@ -7,6 +7,13 @@
 // byte_perm(word, 0x80, 0x?455) then yields the FP32 value +-1.0f directly.
 // Word index: (c * L*L + r) * W + (m >> 2), byte m & 3.
 //
+// Spin storage in HBM (pthr_config.spin_layout): either that byte layout, or
+// one sign bit per byte slot -- bit 4w + k of a lattice's 32-bit bit words
+// (word (4w + k) >> 5, bit (4w + k) & 31) is bit 7 of byte k of packed word w,
+// 1 = spin -1, so one bit word holds eight packed words and row padding is
+// 0.  Kernels that keep lattices in shared memory expand the bits to the byte
+// layout when they stage them and pack them again on write-back.
+//
 // Random numbers: Philox4x32-10 (Salmon et al., SC'11) keyed by the sample's
 // 64-bit seed; counter words (c0, c1, c2, c3) per stream:
 //   init spins  (i>>2, lattice, 0, TAG_INIT)              word i & 3
@@ -53,6 +60,37 @@ __host__ __device__ inline int lattice_words(int L) {
     return 2 * L * L * W;
 }
 
+// 32-bit words per lattice in HBM: the byte layout's words, or an eighth of
+// them in the bit layout (L even makes lattice_words(L) a multiple of 8)
+__host__ __device__ inline int storage_words(int L, int bits) {
+    return bits ? lattice_words(L) / 8 : lattice_words(L);
+}
+
+// bit 7 of the four bytes of w (the sign of a packed spin, or where two
+// packed words differ) as the low four bits; a multiply gathers them
+__device__ __forceinline__ uint32_t sign_nibble(uint32_t w) {
+    return ((w & 0x80808080u) * 0x00204081u) >> 28;
+}
+
+// the inverse: four sign bits as the packed word of their 0x3F / 0xBF bytes
+// (the multiply places bit k at bit 8k; the shifted copies fall elsewhere)
+__device__ __forceinline__ uint32_t expand_nibble(uint32_t n) {
+    return 0x3F3F3F3Fu | (((n * 0x00204081u) & 0x01010101u) << 7);
+}
+
+// Packed words 8u .. 8u+7 of a lattice from its bit word u, and back.
+__device__ __forceinline__ void expand_bits(uint32_t bw, uint4 &lo, uint4 &hi) {
+    lo = make_uint4(expand_nibble(bw & 0xFu), expand_nibble((bw >> 4) & 0xFu),
+                    expand_nibble((bw >> 8) & 0xFu), expand_nibble((bw >> 12) & 0xFu));
+    hi = make_uint4(expand_nibble((bw >> 16) & 0xFu), expand_nibble((bw >> 20) & 0xFu),
+                    expand_nibble((bw >> 24) & 0xFu), expand_nibble(bw >> 28));
+}
+__device__ __forceinline__ uint32_t pack_bits(const uint4 &lo, const uint4 &hi) {
+    return sign_nibble(lo.x) | (sign_nibble(lo.y) << 4) | (sign_nibble(lo.z) << 8) |
+           (sign_nibble(lo.w) << 12) | (sign_nibble(hi.x) << 16) | (sign_nibble(hi.y) << 20) |
+           (sign_nibble(hi.z) << 24) | (sign_nibble(hi.w) << 28);
+}
+
 // Everything a kernel needs about the batch; passed by value.
 struct Batch {
     float *J;                 // [S][3][V]
@@ -77,7 +115,8 @@ struct Batch {
     const double *tabQ;       // [V+1]   (V - 2n) / V
     const double *tabQl;      // [3V+1]  (3V - 2n) / (3V)
     const float *tabTb;       // [NT]    (float)(-2 log2(e) / T_k)
-    int S, L, NT, NR, NRES, NSLOT, NLAT, NPAIR, lat_words;
+    int S, L, NT, NR, NRES, NSLOT, NLAT, NPAIR, lat_words;   // lat_words: storage words
+    int bits;                 // spin storage: 0 bytes, 1 bits (PTHR_SPINS_*)
     int rule, cluster_mode, acu_interval, n_acu;
     double t_min, t_max;
 };

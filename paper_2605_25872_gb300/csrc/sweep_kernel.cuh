@@ -402,8 +402,20 @@ __device__ __forceinline__ void sweep_block(const SweepArgs &a, int bid, unsigne
             }
         }
     }
-    // ---- spins -> shared memory: all K lattices in one flat loop
-    {
+    // ---- spins -> shared memory: all K lattices in one flat loop (bit
+    // storage: one bit word expands to eight packed words)
+    if (b.bits) {
+        constexpr int LB8 = LW / 8;
+        const int nq = K * LB8;
+        for (int i = tid; i < nq; i += T) {
+            const int k = i / LB8;
+            uint4 lo, hi;
+            expand_bits(b.spins[((size_t)s * b.NLAT + s_lat[k]) * LB8 + (i - k * LB8)], lo, hi);
+            uint4 *d = reinterpret_cast<uint4 *>(Ss + k * LW + 8 * (i - k * LB8));
+            d[0] = lo;
+            d[1] = hi;
+        }
+    } else {
         constexpr int LQ = LW / 4;
         const int nq = K * LQ;
         constexpr int SU = 4;
@@ -766,7 +778,15 @@ __device__ __forceinline__ void sweep_block(const SweepArgs &a, int bid, unsigne
     }
     __syncthreads();
     // ---- write back: one flat loop over all K lattices
-    {
+    if (b.bits) {
+        constexpr int LB8 = LW / 8;
+        const int nq = K * LB8;
+        for (int i = tid; i < nq; i += T) {
+            const int k = i / LB8;
+            const uint4 *w = reinterpret_cast<const uint4 *>(Ss + k * LW + 8 * (i - k * LB8));
+            b.spins[((size_t)s * b.NLAT + s_lat[k]) * LB8 + (i - k * LB8)] = pack_bits(w[0], w[1]);
+        }
+    } else {
         constexpr int LQ = LW / 4;
         const int nq = K * LQ;
         for (int i = tid; i < nq; i += T) {

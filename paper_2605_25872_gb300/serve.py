@@ -53,6 +53,7 @@ class PoolSpec:
     sweeps_per_emcs: int = 10
     res_sweeps_per_emcs: int = 240
     pretherm_sweeps: int = 960
+    spin_layout: str = "bytes"      # "bits": 8x less spin memory per slot
 
     def updates_per_emcs_per_sample(self):
         V = self.L ** 3
@@ -72,7 +73,7 @@ class GpuPool:
                                t_min=spec.t_min, t_max=spec.t_max, n_replicas=spec.n_replicas,
                                n_res=spec.n_res, sweeps_per_emcs=spec.sweeps_per_emcs,
                                res_sweeps_per_emcs=spec.res_sweeps_per_emcs,
-                               er_on=spec.n_res > 0, cluster="acu")
+                               er_on=spec.n_res > 0, cluster="acu", spin_layout=spec.spin_layout)
         self.batch = Batch(self.cfg, device=device, stream=self.stream)
         self.batch.set_active(0, spec.slots, False)
         self.graph = graph

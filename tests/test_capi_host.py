@@ -53,15 +53,34 @@ def test_required_bytes_and_layout(lib):
     assert lib.pthr_lattice_bytes(12, ctypes.byref(n)) == 0 and n.value == 2 * 144 * 8
 
 
+def test_bit_spin_storage_sizes(lib):
+    n = ctypes.c_size_t()
+    for L in (2, 4, 6, 12, 16, 24):
+        lib.pthr_lattice_bytes(L, ctypes.byref(n))
+        byte_bytes = n.value
+        assert lib.pthr_lattice_storage_bytes(L, _lib.SPINS_BYTES, ctypes.byref(n)) == 0
+        assert n.value == byte_bytes
+        assert lib.pthr_lattice_storage_bytes(L, _lib.SPINS_BITS, ctypes.byref(n)) == 0
+        assert n.value * 8 == byte_bytes and n.value % 4 == 0
+    assert lib.pthr_lattice_storage_bytes(12, 2, ctypes.byref(n)) == _lib.PTHR_E_INVAL
+    assert lib.pthr_lattice_storage_bytes(13, _lib.SPINS_BITS, ctypes.byref(n)) == _lib.PTHR_E_INVAL
+    c = BatchConfig(L=16, n_samples=512, n_temps=32, spin_layout="bits")
+    assert buffer_info(c, _lib.BUF_SPINS)[1] == 512 * 144 * 512
+    assert required_bytes(c) < required_bytes(BatchConfig(L=16, n_samples=512, n_temps=32)) - 250e6
+
+
 @pytest.mark.parametrize("field,value", [("L", 3), ("L", 26), ("L", 0), ("n_samples", 0),
                                          ("n_temps", 1), ("n_replicas", 0), ("n_replicas", 3),
                                          ("t_min", 0.0), ("t_max", 0.1), ("acu_interval", 0),
-                                         ("n_res", 0), ("rule", "bogus")])
+                                         ("n_res", 0), ("rule", "bogus"), ("spin_layout", 2)])
 def test_invalid_configs_are_rejected(lib, field, value):
     c = BatchConfig(L=8, n_samples=4, n_temps=8)
     if field == "rule":
         cc = c.to_c()
         cc.update_rule = 7
+    elif field == "spin_layout":
+        cc = c.to_c()
+        cc.spin_layout = 2
     else:
         setattr(c, field, value)
         cc = c.to_c()
