@@ -41,6 +41,24 @@ __device__ __forceinline__ int find_root(volatile int *parent, int x, int cap, b
     return x;
 }
 
+// The root of x without writing anything.  For flattening after every join
+// is done: the forest no longer changes, but other threads are writing the
+// final roots, and a path-halving store could replace a final root with an
+// intermediate ancestor after its owner wrote it.
+__device__ __forceinline__ int find_root_readonly(volatile int *parent, int x, int cap, bool &ok,
+                                                  uint32_t *status = nullptr, int V = 0) {
+    for (int it = 0; it < cap; ++it) {
+        const int p = parent[x];
+        if (p == x) return x;
+#ifdef PTHR_DEBUG
+        if (!PTHR_DCHECK(status, p >= 0 && p < V)) { ok = false; return x; }
+#endif
+        x = p;
+    }
+    ok = false;
+    return x;
+}
+
 __device__ __forceinline__ void unite(volatile int *parent, int a, int b, int cap, bool &ok,
                                       uint32_t *status = nullptr, int V = 0) {
     for (int it = 0; it < cap; ++it) {
@@ -238,8 +256,10 @@ __device__ __forceinline__ void cluster_block(const ClusterArgs &a, int bid, uns
         }
     }
     __syncthreads();
+    // every site points straight at its root; only final roots are written
+    // here (no path halving), so after the barrier parent[i] is the root
     for (int i = tid; i < V; i += T) {
-        const int r = find_root(vp, i, cap, ok, b.status, V);
+        const int r = find_root_readonly(vp, i, cap, ok, b.status, V);
         parent[i] = r;
     }
     if (!ok) s_ok = 0;

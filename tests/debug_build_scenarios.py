@@ -1,6 +1,7 @@
 """Scenarios run under both builds of the CUDA library (release and the
 range-checked PTHR_DEBUG build): every step of the EMCS at several lattice
-sizes, both cluster moves, heat bath, pre-thermalisation and labels.
+sizes, both cluster moves, heat bath, MicSA, both spin layouts,
+pre-thermalisation and labels.
 
 Run as a script (python tests/debug_build_scenarios.py OUT.npz) it executes
 the scenarios in this process with whatever library PTHR_LIBRARY names and
@@ -24,6 +25,11 @@ SCENARIOS = [
          rule="heatbath"),
     dict(L=12, n_samples=2, n_temps=6, n_replicas=4, n_res=0, er_on=False, sweeps_per_emcs=1),
     dict(L=16, n_samples=2, n_temps=4, n_replicas=4, n_res=2, sweeps_per_emcs=2, res_sweeps_per_emcs=4),
+    # bit spin storage, padded rows (L = 12) and full rows (L = 8)
+    dict(L=12, n_samples=2, n_temps=6, n_replicas=4, n_res=2, sweeps_per_emcs=1, res_sweeps_per_emcs=3,
+         spin_layout="bits"),
+    dict(L=8, n_samples=2, n_temps=8, n_replicas=4, n_res=2, sweeps_per_emcs=2, res_sweeps_per_emcs=2,
+         rule="micsa", spin_layout="bits"),
 ]
 
 

@@ -1,0 +1,76 @@
+"""Run-to-run determinism at the sizes where concurrency shows.
+
+Every random number is keyed by (sample, lattice, site, step), the energies
+are exact integer sums on the coupling grid and every accumulation runs in a
+fixed order, so two batches with the same inputs must stay bit-identical
+step by step.  Differences would come from a race between threads: the
+union-find of the cluster kernel is the one place where many threads write
+the same shared array, and a path-halving store during flattening once left
+a site pointing at an intermediate ancestor instead of its root (a rare
+wrong flip, seen in one pair out of thousands).  The small parity tests are
+too small to meet such a race; these run many pairs per launch.
+"""
+import numpy as np
+import pytest
+import torch
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+P = pytest.importorskip("paper_2605_25872_gb300")
+from paper_2605_25872_gb300 import Batch, BatchConfig  # noqa: E402
+from paper_2605_25872_gb300.build import build  # noqa: E402
+
+NAMES = ["energies", "perm", "age", "rt_state", "round_trips", "pt_accepted", "flips", "obs", "cluster_stats"]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    build()
+
+
+def state(b):
+    torch.cuda.synchronize()
+    d = {n: getattr(b, n).cpu().numpy().copy() for n in NAMES}
+    d["spins"] = b.export_spins().cpu().numpy()
+    torch.cuda.synchronize()
+    return d
+
+
+def assert_same(a, b, where):
+    for n in a:
+        assert np.array_equal(a[n], b[n]), f"{where}: {n} differs at {np.argwhere(a[n] != b[n])[:5].tolist()}"
+
+
+@pytest.mark.parametrize("L,S,NT,cluster", [(16, 64, 32, "acu"), (12, 160, 24, "acu"), (8, 256, 16, "single")])
+def test_identical_inputs_give_identical_trajectories(L, S, NT, cluster):
+    cfg = BatchConfig(L=L, n_samples=S, n_temps=NT, n_replicas=4, n_res=4 if L == 16 else 0,
+                      sweeps_per_emcs=10 if L == 16 else 1, res_sweeps_per_emcs=240 if L == 16 else 0,
+                      er_on=L == 16, cluster=cluster)
+    J = W.gaussian_couplings(L, S, 5)
+    seeds = W.sample_seeds(W.SEED_BASE + 5, S)
+    st = torch.cuda.Stream()
+    bs = [Batch(cfg, couplings=J, seeds=seeds, stream=st) for _ in range(2)]
+    if cfg.er_on:
+        for b in bs:
+            b.prethermalize(240)
+    for e in range(3 if L == 16 else 12):
+        for b in bs:
+            b.sweep(cfg.sweeps_per_emcs, cfg.res_sweeps_per_emcs if cfg.er_on else 0)
+            b.houdayer()
+        assert_same(state(bs[0]), state(bs[1]), f"EMCS {e} after the cluster move")
+        for b in bs:
+            b.swap(True, cfg.er_on)
+            b.measure()
+    la, lb = (b.cluster_labels().cpu().numpy() for b in bs)
+    np.testing.assert_array_equal(la, lb)
+    # canonical labels: every label is a site labelled by itself, no larger than the site
+    flat = la.reshape(-1, cfg.V)
+    i = np.arange(cfg.V)
+    assert np.all(flat <= i)
+    assert np.all(np.take_along_axis(flat, flat, axis=1) == flat)
+    for b in bs:
+        assert b.poll(60000) == 0
