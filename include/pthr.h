@@ -297,10 +297,12 @@ PTHR_API pthr_status pthr_set_active(pthr_batch *b, int first, int count, int ac
  * cluster move, the swap and the measurement of every batch, each step one
  * kernel over the blocks of all batches; otherwise it holds each batch's own
  * EMCS on its own stream, forked from and joined to `stream`.
- * pthr_group_emcs replays the graph n times on `stream`.  The batches must be
- * at an EMCS boundary, must not be destroyed before the group, and their
- * idle slots cost no work.  Kernel shapes are fixed at creation.  Results
- * are those of stepping every batch alone. */
+ * pthr_group_emcs replays the graph n times on `stream`, after the work
+ * already queued on every member's own stream and before the work queued on
+ * them later (events), so per-batch calls and group EMCS may be mixed.  The
+ * batches must be at an EMCS boundary, must not be destroyed before the
+ * group, and their idle slots cost no work.  Kernel shapes are fixed at
+ * creation.  Results are those of stepping every batch alone. */
 typedef struct pthr_group pthr_group;
 PTHR_API pthr_status pthr_group_create(pthr_batch *const *batches, int n, void *stream,
                                        pthr_group **out);

@@ -720,7 +720,43 @@ struct pthr_group {
     cudaGraphExec_t exec;
     int n;
     int launches;   // kernel launches per EMCS in the graph
+    pthr_batch **batches;   // [n] members, for ordering against their own streams
+    cudaEvent_t *ev_in;     // [n] work queued on each member's stream
+    cudaEvent_t ev_out;     // the group's EMCS, for the members' later work
 };
+
+namespace {
+
+// A new group handle with its ordering events; nullptr if an event could not
+// be created (then nothing is left allocated).
+pthr_group *new_group(pthr_batch *const *batches, int n, cudaStream_t st, cudaGraph_t g, cudaGraphExec_t exec,
+                      int launches) {
+    pthr_group *grp = new pthr_group();
+    grp->stream = st;
+    grp->graph = g;
+    grp->exec = exec;
+    grp->n = n;
+    grp->launches = launches;
+    grp->batches = new pthr_batch *[n];
+    grp->ev_in = new cudaEvent_t[n]();
+    grp->ev_out = nullptr;
+    bool ok = cudaEventCreateWithFlags(&grp->ev_out, cudaEventDisableTiming) == cudaSuccess;
+    for (int i = 0; i < n; ++i) {
+        grp->batches[i] = batches[i];
+        ok = ok && cudaEventCreateWithFlags(&grp->ev_in[i], cudaEventDisableTiming) == cudaSuccess;
+    }
+    if (!ok) {
+        for (int i = 0; i < n; ++i) if (grp->ev_in[i]) cudaEventDestroy(grp->ev_in[i]);
+        if (grp->ev_out) cudaEventDestroy(grp->ev_out);
+        delete[] grp->ev_in;
+        delete[] grp->batches;
+        delete grp;
+        return nullptr;
+    }
+    return grp;
+}
+
+}  // namespace
 
 namespace {
 
@@ -831,12 +867,12 @@ PTHR_API pthr_status pthr_group_create(pthr_batch *const *batches, int n, void *
             cudaGraphExec_t exec = nullptr;
             e = cudaGraphInstantiate(&exec, g, 0);
             if (e != cudaSuccess) { cudaGraphDestroy(g); return cuda_fail(nullptr, e, "group graph instantiate"); }
-            pthr_group *grp = new pthr_group();
-            grp->stream = master;
-            grp->graph = g;
-            grp->exec = exec;
-            grp->n = n;
-            grp->launches = launches;
+            pthr_group *grp = new_group(batches, n, master, g, exec, launches);
+            if (!grp) {
+                cudaGraphExecDestroy(exec);
+                cudaGraphDestroy(g);
+                return fail(nullptr, PTHR_E_CUDA, "group event create");
+            }
             *out = grp;
             return PTHR_OK;
         }
@@ -876,14 +912,15 @@ PTHR_API pthr_status pthr_group_create(pthr_batch *const *batches, int n, void *
         if (st != PTHR_OK) return fail(nullptr, st, "batch %d: %s", failed, batches[failed]->err);
         return cuda_fail(nullptr, e, "group capture");
     }
-    pthr_group *grp = new pthr_group();
-    grp->stream = master;
-    grp->graph = g;
-    grp->exec = exec;
-    grp->n = n;
-    grp->launches = 0;
+    int launches = 0;
     for (int i = 0; i < n; ++i)
-        grp->launches += 2 + (batches[i]->cfg.cluster_mode != PTHR_CLUSTER_OFF && batches[i]->dev.n_acu > 0) + 1;
+        launches += 2 + (batches[i]->cfg.cluster_mode != PTHR_CLUSTER_OFF && batches[i]->dev.n_acu > 0) + 1;
+    pthr_group *grp = new_group(batches, n, master, g, exec, launches);
+    if (!grp) {
+        cudaGraphExecDestroy(exec);
+        cudaGraphDestroy(g);
+        return fail(nullptr, PTHR_E_CUDA, "group event create");
+    }
     *out = grp;
     return PTHR_OK;
 }
@@ -896,10 +933,21 @@ PTHR_API pthr_status pthr_group_info(const pthr_group *g, int *launches_per_emcs
 
 PTHR_API pthr_status pthr_group_emcs(pthr_group *g, int n) {
     if (!g || n < 0) return fail(nullptr, PTHR_E_INVAL, "bad group or count");
+    if (n == 0) return PTHR_OK;
+    // after the work already queued on every member's stream ...
+    for (int i = 0; i < g->n; ++i) {
+        cudaError_t e = cudaEventRecord(g->ev_in[i], g->batches[i]->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(g->stream, g->ev_in[i], 0);
+        if (e != cudaSuccess) return cuda_fail(nullptr, e, "group ordering");
+    }
     for (int i = 0; i < n; ++i) {
         cudaError_t e = cudaGraphLaunch(g->exec, g->stream);
         if (e != cudaSuccess) return cuda_fail(nullptr, e, "group graph launch");
     }
+    // ... and before the work queued on them later
+    cudaError_t e = cudaEventRecord(g->ev_out, g->stream);
+    for (int i = 0; i < g->n && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(g->batches[i]->stream, g->ev_out, 0);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "group ordering");
     return PTHR_OK;
 }
 
@@ -907,6 +955,10 @@ PTHR_API void pthr_group_destroy(pthr_group *g) {
     if (!g) return;
     if (g->exec) cudaGraphExecDestroy(g->exec);
     if (g->graph) cudaGraphDestroy(g->graph);
+    for (int i = 0; i < g->n; ++i) if (g->ev_in[i]) cudaEventDestroy(g->ev_in[i]);
+    if (g->ev_out) cudaEventDestroy(g->ev_out);
+    delete[] g->ev_in;
+    delete[] g->batches;
     delete g;
 }
 

@@ -45,11 +45,13 @@ def assert_same(a, b, where):
         assert np.array_equal(a[n], b[n]), f"{where}: {n} differs at {np.argwhere(a[n] != b[n])[:5].tolist()}"
 
 
-@pytest.mark.parametrize("L,S,NT,cluster", [(16, 64, 32, "acu"), (12, 160, 24, "acu"), (8, 256, 16, "single")])
-def test_identical_inputs_give_identical_trajectories(L, S, NT, cluster):
+@pytest.mark.parametrize("L,S,NT,cluster,rule", [(16, 64, 32, "acu", "metropolis"), (12, 160, 24, "acu", "metropolis"),
+                                                  (8, 256, 16, "single", "metropolis"), (16, 48, 32, "acu", "micsa"),
+                                                  (10, 128, 24, "acu", "heatbath")])
+def test_identical_inputs_give_identical_trajectories(L, S, NT, cluster, rule):
     cfg = BatchConfig(L=L, n_samples=S, n_temps=NT, n_replicas=4, n_res=4 if L == 16 else 0,
                       sweeps_per_emcs=10 if L == 16 else 1, res_sweeps_per_emcs=240 if L == 16 else 0,
-                      er_on=L == 16, cluster=cluster)
+                      er_on=L == 16, cluster=cluster, rule=rule)
     J = W.gaussian_couplings(L, S, 5)
     seeds = W.sample_seeds(W.SEED_BASE + 5, S)
     st = torch.cuda.Stream()
@@ -74,3 +76,62 @@ def test_identical_inputs_give_identical_trajectories(L, S, NT, cluster):
     assert np.all(np.take_along_axis(flat, flat, axis=1) == flat)
     for b in bs:
         assert b.poll(60000) == 0
+
+
+def test_identical_groups_give_identical_trajectories():
+    """The four-launch group of the serving mix: every kernel covers the blocks
+    of five batches at once."""
+    from paper_2605_25872_gb300.batch import Group
+    groups = []
+    for _ in range(2):
+        bs = []
+        for i, L in enumerate((6, 8, 10, 12, 16)):
+            cfg = BatchConfig(L=L, n_samples=32, n_temps=24, n_replicas=4, n_res=4, sweeps_per_emcs=10,
+                              res_sweeps_per_emcs=240)
+            bs.append(Batch(cfg, couplings=W.gaussian_couplings(L, 32, 40 + i),
+                            seeds=W.sample_seeds(W.SEED_BASE + 40 + i, 32), stream=torch.cuda.Stream()))
+            bs[-1].prethermalize(240)
+        torch.cuda.synchronize()
+        g = Group(bs)
+        assert g.launches_per_emcs == 4
+        groups.append((g, bs))
+    for e in range(3):
+        for g, _ in groups:
+            g.emcs(1)
+            g.synchronize()
+        for a, b in zip(groups[0][1], groups[1][1]):
+            assert_same(state(a), state(b), f"EMCS {e}, L={a.cfg.L}")
+
+
+def test_group_emcs_is_ordered_with_the_members_streams():
+    """Per-batch calls and group EMCS mixed without host synchronisation give
+    the state of the same calls with a synchronisation after each."""
+    from paper_2605_25872_gb300.batch import Group
+
+    def members():
+        out = []
+        for i, L in enumerate((8, 12)):
+            cfg = BatchConfig(L=L, n_samples=24, n_temps=16, n_replicas=4, n_res=4, sweeps_per_emcs=4,
+                              res_sweeps_per_emcs=96)
+            out.append(Batch(cfg, couplings=W.gaussian_couplings(L, 24, 60 + i),
+                             seeds=W.sample_seeds(W.SEED_BASE + 60 + i, 24), stream=torch.cuda.Stream()))
+        torch.cuda.synchronize()
+        return out
+
+    free, synced = members(), members()
+    gf, gs = Group(free), Group(synced)
+    for b in free:
+        b.prethermalize(480)          # still running when the group EMCS is queued
+    gf.emcs(2)
+    for b in free:
+        b.emcs(1)                     # queued on the member streams after the group EMCS
+    for b in synced:
+        b.prethermalize(480)
+    torch.cuda.synchronize()
+    gs.emcs(2)
+    torch.cuda.synchronize()
+    for b in synced:
+        b.emcs(1)
+    torch.cuda.synchronize()
+    for a, b in zip(free, synced):
+        assert_same(state(a), state(b), f"L={a.cfg.L}")
