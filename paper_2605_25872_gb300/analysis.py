@@ -108,3 +108,39 @@ def spin_autocorrelation(sums, n_replicas: int, n_res: int, V: int):
     n = c.shape[0]
     err = c.std(axis=0, ddof=1) / np.sqrt(n) if n > 1 else np.full(c.shape[1], np.nan)
     return c, c.mean(axis=0), err
+
+
+def observable_records(obs: np.ndarray, T, n_replicas: int, emcs: int, sample_ids=None,
+                       pt_accepted=None, cluster_stats=None) -> list:
+    """One flat record per (sample, temperature) of the thermal averages of
+    `thermal_averages` at EMCS count `emcs`, for logging as JSON lines.
+    Optional: PT acceptance counts [S, N_r, N_T] (summed over groups, pair
+    (k, k+1) on temperature k) and the last cluster move's statistics
+    [S, n_pairs, N_T, 4] (clusters, largest, second largest, flipped sites;
+    summed over pairs)."""
+    avg = thermal_averages(np.asarray(obs, dtype=np.float64), n_replicas)
+    S, NT = obs.shape[:2]
+    ids = list(range(S)) if sample_ids is None else [int(x) for x in sample_ids]
+    out = []
+    for s in range(S):
+        for k in range(NT):
+            rec = {"emcs": int(emcs), "sample": ids[s], "k": k, "T": float(T[k]),
+                   "n": int(obs[s, k, N])}
+            rec.update({name: float(v[s, k]) for name, v in avg.items()})
+            if pt_accepted is not None:
+                rec["pt_accepted"] = int(np.asarray(pt_accepted)[s, :, k].sum())
+            if cluster_stats is not None:
+                cs = np.asarray(cluster_stats)[s, :, k].sum(axis=0)
+                rec.update({"clusters": int(cs[0]), "largest": int(cs[1]), "second": int(cs[2]),
+                            "flipped": int(cs[3])})
+            out.append(rec)
+    return out
+
+
+def append_jsonl(path, records) -> int:
+    """Append records (dicts) to a JSON-lines file; returns the count."""
+    import json
+    with open(path, "a") as f:
+        for r in records:
+            f.write(json.dumps(r) + "\n")
+    return len(records)

@@ -1,6 +1,8 @@
 // capi.cu -- the extern "C" boundary declared in include/pthr.h: configuration
 // checks, workspace layout, launch shapes, EMCS schedule, CUDA-graph replay,
-// device-status polling and checkpoints.
+// device-status polling and checkpoints.  Every entry point that enqueues
+// GPU work opens an NVTX range named after itself (a no-op unless a
+// profiler is attached), so traces show the C-ABI calls around the kernels.
 #include <chrono>
 #include <cstdarg>
 #include <cstdio>
@@ -8,9 +10,22 @@
 #include <vector>
 #include <thread>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "kernels.cuh"
 
 using namespace pthr;
+
+namespace {
+// NVTX range for the lifetime of one C-ABI call
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
+}  // namespace
+#define PTHR_TRACE(name) const NvtxRange pthr_nvtx_range_(name)
 
 struct pthr_batch {
     pthr_config cfg;
@@ -351,6 +366,7 @@ PTHR_API pthr_status pthr_lattice_storage_bytes(int L, int spin_layout, size_t *
 PTHR_API pthr_status pthr_create_batch(const pthr_config *cfg, void *device_workspace, size_t workspace_bytes,
                                        const float *couplings, const uint64_t *seeds, void *stream,
                                        pthr_batch **out) {
+    PTHR_TRACE("pthr_create_batch");
     pthr_status st = check_config(cfg);
     if (st != PTHR_OK) return st;
     if (!out) return fail(nullptr, PTHR_E_INVAL, "out is NULL");
@@ -502,6 +518,7 @@ PTHR_API pthr_status pthr_get_tuning(const pthr_batch *b, pthr_tuning *t) {
 }
 
 PTHR_API pthr_status pthr_sweep(pthr_batch *b, int n_pt_sweeps, int n_res_sweeps) {
+    PTHR_TRACE("pthr_sweep");
     if (!b) return fail(nullptr, PTHR_E_INVAL, "NULL handle");
     if (n_pt_sweeps < 0 || n_res_sweeps < 0) return fail(b, PTHR_E_INVAL, "negative sweep count");
     if ((long)b->pt_sweep_off + n_pt_sweeps >= (1L << 23) || (long)b->res_sweep_off + n_res_sweeps >= (1L << 23))
@@ -515,17 +532,20 @@ PTHR_API pthr_status pthr_sweep(pthr_batch *b, int n_pt_sweeps, int n_res_sweeps
 }
 
 PTHR_API pthr_status pthr_houdayer(pthr_batch *b) {
+    PTHR_TRACE("pthr_houdayer");
     if (!b) return fail(nullptr, PTHR_E_INVAL, "NULL handle");
     if (b->cfg.cluster_mode == PTHR_CLUSTER_OFF) return PTHR_OK;
     return do_cluster(b, 0, nullptr);
 }
 
 PTHR_API pthr_status pthr_cluster_labels(pthr_batch *b, int32_t *out_device) {
+    PTHR_TRACE("pthr_cluster_labels");
     if (!b || !out_device) return fail(b, PTHR_E_INVAL, "NULL argument");
     return do_cluster(b, 1, out_device);
 }
 
 PTHR_API pthr_status pthr_swap(pthr_batch *b, int flags) {
+    PTHR_TRACE("pthr_swap");
     if (!b) return fail(nullptr, PTHR_E_INVAL, "NULL handle");
     if (flags & ~(PTHR_SWAP_PT | PTHR_SWAP_ER)) return fail(b, PTHR_E_INVAL, "unknown swap flags");
     if ((flags & PTHR_SWAP_ER) && b->cfg.n_res < 1) return fail(b, PTHR_E_INVAL, "ER needs n_res >= 1");
@@ -536,6 +556,7 @@ PTHR_API pthr_status pthr_swap(pthr_batch *b, int flags) {
 }
 
 PTHR_API pthr_status pthr_observables(pthr_batch *b, int flags, void *out, size_t bytes) {
+    PTHR_TRACE("pthr_observables");
     if (!b) return fail(nullptr, PTHR_E_INVAL, "NULL handle");
     const size_t need = (size_t)b->cfg.n_samples * b->cfg.n_temps * PTHR_NOBS * sizeof(double);
     if ((flags & (PTHR_OBS_READ_HOST | PTHR_OBS_READ_DEVICE)) && (!out || bytes < need))
@@ -558,6 +579,7 @@ PTHR_API pthr_status pthr_observables(pthr_batch *b, int flags, void *out, size_
 }
 
 PTHR_API pthr_status pthr_emcs(pthr_batch *b, int n, int use_graph) {
+    PTHR_TRACE("pthr_emcs");
     if (!b) return fail(nullptr, PTHR_E_INVAL, "NULL handle");
     if (n < 0) return fail(b, PTHR_E_INVAL, "negative EMCS count");
     if (b->pt_sweep_off || b->res_sweep_off)
@@ -588,6 +610,7 @@ PTHR_API pthr_status pthr_emcs(pthr_batch *b, int n, int use_graph) {
 }
 
 PTHR_API pthr_status pthr_prethermalize_reservoir(pthr_batch *b, int first, int count, int n_sweeps) {
+    PTHR_TRACE("pthr_prethermalize_reservoir");
     if (!b) return fail(nullptr, PTHR_E_INVAL, "NULL handle");
     if (first < 0 || count < 0 || first + count > b->cfg.n_samples || n_sweeps < 0 || n_sweeps >= (1 << 23))
         return fail(b, PTHR_E_INVAL, "bad sample range or sweep count");
@@ -622,12 +645,14 @@ PTHR_API pthr_status pthr_poll(pthr_batch *b, int timeout_ms) {
 }
 
 PTHR_API pthr_status pthr_export_spins(pthr_batch *b, int8_t *out_device) {
+    PTHR_TRACE("pthr_export_spins");
     if (!b || !out_device) return fail(b, PTHR_E_INVAL, "NULL argument");
     CUDA_TRY(b, launch_export_spins(b->dev, out_device, b->stream), "export launch");
     return PTHR_OK;
 }
 
 PTHR_API pthr_status pthr_import_spins(pthr_batch *b, const int8_t *in_device) {
+    PTHR_TRACE("pthr_import_spins");
     if (!b || !in_device) return fail(b, PTHR_E_INVAL, "NULL argument");
     CUDA_TRY(b, launch_import_spins(b->dev, in_device, b->stream), "import launch");
     return do_sweep(b, 0, 0, 0, b->cfg.n_samples, 0);
@@ -635,6 +660,7 @@ PTHR_API pthr_status pthr_import_spins(pthr_batch *b, const int8_t *in_device) {
 
 PTHR_API pthr_status pthr_reset_samples(pthr_batch *b, int first, int count, const float *couplings,
                                         const uint64_t *seeds, int pretherm_sweeps) {
+    PTHR_TRACE("pthr_reset_samples");
     if (!b) return fail(nullptr, PTHR_E_INVAL, "NULL handle");
     if (first < 0 || count < 1 || first + count > b->cfg.n_samples || !seeds || pretherm_sweeps < 0)
         return fail(b, PTHR_E_INVAL, "bad sample range, seeds or pre-thermalisation");
@@ -679,6 +705,7 @@ struct BlobHeader {
 };
 
 PTHR_API pthr_status pthr_save(pthr_batch *b, void *blob, size_t *bytes) {
+    PTHR_TRACE("pthr_save");
     if (!b || !bytes) return fail(b, PTHR_E_INVAL, "NULL argument");
     const size_t total = make_layout(&b->cfg).total;
     const size_t need = sizeof(BlobHeader) + total;
@@ -699,6 +726,7 @@ PTHR_API pthr_status pthr_save(pthr_batch *b, void *blob, size_t *bytes) {
 }
 
 PTHR_API pthr_status pthr_load(pthr_batch *b, const void *blob, size_t bytes) {
+    PTHR_TRACE("pthr_load");
     if (!b || !blob) return fail(b, PTHR_E_INVAL, "NULL argument");
     BlobHeader h;
     if (bytes < sizeof(h)) return fail(b, PTHR_E_INVAL, "blob too small");
@@ -843,6 +871,7 @@ pthr_status group_fused_emcs(pthr_batch *const *batches, int n, cudaStream_t st,
 }  // namespace
 
 PTHR_API pthr_status pthr_group_create(pthr_batch *const *batches, int n, void *stream, pthr_group **out) {
+    PTHR_TRACE("pthr_group_create");
     if (!batches || n < 1 || !out || !stream)
         return fail(nullptr, PTHR_E_INVAL, "group needs batches, n >= 1, a non-default stream and out");
     *out = nullptr;
@@ -932,6 +961,7 @@ PTHR_API pthr_status pthr_group_info(const pthr_group *g, int *launches_per_emcs
 }
 
 PTHR_API pthr_status pthr_group_emcs(pthr_group *g, int n) {
+    PTHR_TRACE("pthr_group_emcs");
     if (!g || n < 0) return fail(nullptr, PTHR_E_INVAL, "bad group or count");
     if (n == 0) return PTHR_OK;
     // after the work already queued on every member's stream ...
@@ -967,6 +997,7 @@ PTHR_API const char *pthr_last_error(const pthr_batch *b) { return b ? b->err : 
 PTHR_API pthr_status pthr_reservoir_autocorrelation(pthr_batch *b, int first, int count, int n_points,
                                                     int sweeps_per_point, void *snapshot_device,
                                                     size_t snapshot_bytes, int64_t *out_device) {
+    PTHR_TRACE("pthr_reservoir_autocorrelation");
     if (!b) return fail(nullptr, PTHR_E_INVAL, "NULL handle");
     if (b->cfg.n_res < 1) return fail(b, PTHR_E_INVAL, "the batch has no reservoir clones");
     if (first < 0 || count < 1 || first + count > b->cfg.n_samples || n_points < 1 || sweeps_per_point < 1 ||
@@ -991,6 +1022,7 @@ PTHR_API pthr_status pthr_reservoir_autocorrelation(pthr_batch *b, int first, in
 
 PTHR_API pthr_status pthr_reservoir_autocorrelation_noalloc(pthr_batch *b, int first, int count, int n_points,
                                                             int sweeps_per_point, int64_t *out_device) {
+    PTHR_TRACE("pthr_reservoir_autocorrelation_noalloc");
     if (!b) return fail(nullptr, PTHR_E_INVAL, "NULL handle");
     if (b->cfg.n_res < 1) return fail(b, PTHR_E_INVAL, "the batch has no reservoir clones");
     if (first < 0 || count < 1 || first + count > b->cfg.n_samples || n_points < 1 || sweeps_per_point < 1 ||

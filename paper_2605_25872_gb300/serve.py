@@ -35,6 +35,7 @@ class Request:
     finished: float | None = None
     obs: np.ndarray | None = None         # accumulators [n_temps, 8]
     round_trips: np.ndarray | None = None
+    cancelled: bool = False               # withdrawn before its budget was done
 
     @property
     def latency(self):
@@ -145,8 +146,12 @@ class Server:
     the pools whose chunk has finished; pools on different streams overlap
     on the device."""
 
-    def __init__(self, specs, pool_factory=None, clock=None, max_chunk=64):
+    def __init__(self, specs, pool_factory=None, clock=None, max_chunk=64, max_queue=None):
         self.specs = {s.L: s for s in specs}
+        self.max_queue = max_queue          # waiting requests per lattice size; None: unbounded
+        self.refused = []
+        self.cancelled = []
+        self.cancel_requests = deque()      # rids to withdraw, applied by the run loop
         self.pool_factory = pool_factory or (lambda spec: GpuPool(spec))
         self.max_chunk = max(1, int(max_chunk))
         self.pools = {L: self.pool_factory(s) for L, s in self.specs.items()}
@@ -163,10 +168,41 @@ class Server:
     def now(self):
         return self.clock() - self.t0
 
-    def submit(self, req: Request):
+    def submit(self, req: Request) -> bool:
+        """Queue a request; False (refused, nothing queued) when its size's
+        queue already holds max_queue requests."""
         if req.L not in self.specs:
             raise ValueError(f"no pool for L={req.L}")
+        if self.max_queue is not None and len(self.queue[req.L]) >= self.max_queue:
+            self.refused.append(req)
+            return False
         self.queue[req.L].append(req)
+        return True
+
+    def cancel(self, rid: int) -> bool:
+        """Withdraw request rid.  A waiting request leaves its queue at once;
+        a running one is marked and its slot is freed the next time its pool
+        has no chunk in flight (the chunk already queued still advances it;
+        its result is discarded).  False if rid is neither waiting nor
+        running."""
+        for L, q in self.queue.items():
+            for req in q:
+                if req.rid == rid:
+                    q.remove(req)
+                    req.cancelled = True
+                    req.finished = self.now() if self.t0 is not None else None
+                    self.cancelled.append(req)
+                    return True
+        for slots in self.slot_req.values():
+            for req in slots:
+                if req is not None and req.rid == rid and not req.cancelled:
+                    req.cancelled = True
+                    return True
+        return False
+
+    def request_cancel(self, rid: int):
+        """cancel(rid) from another thread: applied by the run loop."""
+        self.cancel_requests.append(rid)
 
     def _admit(self, L):
         q = self.queue[L]
@@ -190,10 +226,17 @@ class Server:
             self.remaining[L][slot] = req.budget_emcs
 
     def _complete(self, L):
-        """Read back and free the slots whose budget is done (pool L idle)."""
+        """Read back and free the slots whose budget is done, and free the
+        cancelled ones (pool L idle)."""
         pool, rem = self.pools[L], self.remaining[L]
         for slot, req in enumerate(self.slot_req[L]):
-            if req is not None and rem[slot] == 0:
+            if req is not None and req.cancelled:
+                req.finished = self.now()
+                pool.free(slot)
+                self.slot_req[L][slot] = None
+                rem[slot] = 0
+                self.cancelled.append(req)
+            elif req is not None and rem[slot] == 0:
                 req.obs, req.round_trips = pool.read(slot)
                 req.finished = self.now()
                 pool.free(slot)
@@ -252,6 +295,8 @@ class Server:
             now = self.now()
             while pending and (not realtime or pending[0].arrival <= now):
                 self.submit(pending.popleft())
+            while self.cancel_requests:
+                self.cancel(self.cancel_requests.popleft())
             progressed = False
             for L, pool in self.pools.items():
                 if self.in_flight[L]:
@@ -277,4 +322,5 @@ class Server:
                 "p99_s": float(np.percentile(lat, 99)) if len(lat) else None,
                 "makespan_s": span,
                 "updates_per_ns": upd / (span * 1e9) if span > 0 else None,
-                "emcs_steps": dict(self.emcs_steps), "chunks": dict(self.chunks)}
+                "emcs_steps": dict(self.emcs_steps), "chunks": dict(self.chunks),
+                "refused": len(self.refused), "cancelled": len(self.cancelled)}

@@ -40,3 +40,26 @@ def test_thermal_averages_and_sdy():
     np.testing.assert_allclose(avg["ql"][0], [0.9, 0.5])
     S = A.sdy(avg["e"][0], avg["ql"][0], np.array([0.5, 1.0]))
     np.testing.assert_allclose(S, [-1 / 3 + 0.2, -0.5 / 3 + 0.5])
+
+
+def test_observable_records_and_jsonl(tmp_path):
+    import json
+    from paper_2605_25872_gb300.analysis import append_jsonl, observable_records
+    S, NT, NR = 2, 3, 4
+    obs = np.zeros((S, NT, 8))
+    obs[..., 0] = 5                               # five measurements
+    obs[..., 1] = -1.5 * 5 * NR                   # <e> = -1.5 over 5 x 4 groups
+    obs[..., 4] = 0.25 * 5 * (NR // 2)            # <q^2> = 0.25 over 5 x 2 pairs
+    pt = np.ones((S, NR, NT), dtype=np.int64)
+    cs = np.tile(np.array([3, 40, 10, 20]), (S, NR // 2, NT, 1))
+    recs = observable_records(obs, [0.2, 0.9, 1.6], NR, emcs=7, sample_ids=[10, 11], pt_accepted=pt,
+                              cluster_stats=cs)
+    assert len(recs) == S * NT
+    r = recs[4]                                   # sample index 1, k = 1
+    assert r["sample"] == 11 and r["k"] == 1 and r["T"] == 0.9 and r["emcs"] == 7 and r["n"] == 5
+    assert r["e"] == -1.5 and r["q2"] == 0.25
+    assert r["pt_accepted"] == NR and r["clusters"] == 6 and r["largest"] == 80
+    path = tmp_path / "obs.jsonl"
+    assert append_jsonl(path, recs) == 6 and append_jsonl(path, recs[:1]) == 1
+    lines = path.read_text().splitlines()
+    assert len(lines) == 7 and json.loads(lines[4]) == r

@@ -91,3 +91,41 @@ def test_unknown_lattice_size_is_rejected():
     except ValueError:
         return
     raise AssertionError("expected ValueError")
+
+
+def test_admission_is_refused_when_the_queue_is_full():
+    srv = Server([PoolSpec(L=6, slots=1)], pool_factory=FakePool, max_queue=2)
+    ok = [srv.submit(Request(rid=i, L=6, seed=i, budget_emcs=2)) for i in range(4)]
+    assert ok == [True, True, False, False]
+    assert [r.rid for r in srv.refused] == [2, 3]
+    done = srv.run([], realtime=False)
+    assert sorted(r.rid for r in done) == [0, 1]
+    assert srv.stats()["refused"] == 2
+
+
+def test_cancel_a_waiting_and_a_running_request():
+    srv = Server([PoolSpec(L=6, slots=1)], pool_factory=FakePool, max_chunk=4)
+    srv.t0 = srv.clock()
+    for i, budget in enumerate((10, 3, 3)):
+        srv.submit(Request(rid=i, L=6, seed=i, budget_emcs=budget))
+    assert srv.cancel(2)                     # still waiting: leaves the queue
+    assert [r.rid for r in srv.queue[6]] == [0, 1]
+    srv._service(6)                          # admits rid 0, enqueues a chunk of 4
+    assert srv.slot_req[6][0].rid == 0
+    assert srv.cancel(0)                     # running: freed at the next service point
+    srv._service(6)                          # frees slot 0, admits rid 1
+    assert srv.slot_req[6][0].rid == 1
+    done = srv.run([], realtime=False)
+    assert [r.rid for r in done] == [1] and done[0].obs[0][1] == 3
+    assert sorted(r.rid for r in srv.cancelled) == [0, 2] and all(r.cancelled for r in srv.cancelled)
+    assert not srv.cancel(1) and not srv.cancel(7)
+    assert srv.stats()["cancelled"] == 2
+
+
+def test_cancel_requested_from_outside_the_loop():
+    srv = Server([PoolSpec(L=6, slots=2)], pool_factory=FakePool)
+    reqs = [Request(rid=i, L=6, seed=i, budget_emcs=5) for i in range(3)]
+    srv.request_cancel(1)
+    done = srv.run(reqs, realtime=False)
+    assert sorted(r.rid for r in done) == [0, 2]
+    assert [r.rid for r in srv.cancelled] == [1]
