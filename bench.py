@@ -439,7 +439,7 @@ def run_gpu(args):
         serving = mixed = micsa = None
         if WL is W.WORKLOADS["c4"] and world == 1:
             serving = serve_measure(args.serve_budget, args.serve_requests, args.serve_mem_gb,
-                                    args.serve_max_slots, args.serve_chunk)
+                                    args.serve_max_slots, args.serve_chunk, not args.serve_default_shapes)
             mixed = mixed_group_measure(dev)
             micsa = micsa_measure(dev, J, seeds)
         result = {
@@ -545,7 +545,7 @@ def end_to_end(dev, cfg, J, seeds, steps):
                         f"{steps} EMCS, D2H observables after every EMCS"}
 
 
-def serve_measure(budget, n_req, mem_gb, max_slots, max_chunk):
+def serve_measure(budget, n_req, mem_gb, max_slots, max_chunk, tuned=True):
     """Serving: Poisson stream of single-sample requests with L uniform in
     {6, 8, 10, 12, 16} (24 temperatures 0.2..1.6, 4 replicas + 4 reservoir
     clones, paper EMCS), admitted into per-L resident pools sized from a
@@ -561,6 +561,13 @@ def serve_measure(budget, n_req, mem_gb, max_slots, max_chunk):
         one = required_bytes(BatchConfig(L=L, n_samples=1, n_temps=24, spin_layout=SPINS))
         slots = int(min(max_slots, (mem / len(W.SERVE_SIZES)) // one))
         specs.append(PoolSpec(L=L, slots=slots, n_temps=24, spin_layout=SPINS))
+    if tuned:
+        # each pool's autotuned kernel shape (measured on this GPU for that
+        # pool's configuration; shapes never change results)
+        from paper_2605_25872_gb300.autotune import autotune
+        from paper_2605_25872_gb300.serve import GpuPool
+        for sp in specs:
+            sp.tuning = autotune(GpuPool.config_of(sp)) or None
     # capacity probe: every pool full, EMCS timed with all pools in flight
     srv = Server(specs, max_chunk=max_chunk)
     probe = [Request(rid=-1 - i * 100000 - k, L=sp.L, seed=10 ** 6 + i * 100000 + k, budget_emcs=10 ** 6)
@@ -582,6 +589,7 @@ def serve_measure(budget, n_req, mem_gb, max_slots, max_chunk):
             "capacity_per_s": cap, "full_pool_emcs_s": per_emcs_s,
             "slots": {sp.L: sp.slots for sp in specs}, "memory_budget_gb": mem_gb,
             "emcs_steps": st["emcs_steps"], "chunks": st["chunks"], "max_chunk": max_chunk,
+            "pool_shapes": {sp.L: (sp.tuning or "default") for sp in specs},
             "config": {"workload": "serving: L uniform in {6,8,10,12,16}, 24 T 0.2..1.6, 4 replicas + "
                                    "4 reservoir clones, paper EMCS, couplings drawn on the device from each "
                                    "request's seed, 960-sweep reservoir pre-thermalisation at admission, "
@@ -701,7 +709,8 @@ def run_serve(args):
     build()
     torch.cuda.set_device(0)
     line = {"mode": "serve", **serve_measure(args.serve_budget, args.serve_requests, args.serve_mem_gb,
-                                             args.serve_max_slots, args.serve_chunk)}
+                                             args.serve_max_slots, args.serve_chunk,
+                                             not args.serve_default_shapes)}
     print(json.dumps(line))
     return 0
 
@@ -733,6 +742,8 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=200)
     ap.add_argument("--serve-mem-gb", type=float, default=2.0)
     ap.add_argument("--serve-max-slots", type=int, default=128)
+    ap.add_argument("--serve-default-shapes", action="store_true",
+                    help="serving pools keep the library's default kernel shapes (else autotuned)")
     ap.add_argument("--serve-chunk", type=int, default=64,
                     help="most EMCS a pool runs between two host checks (serving)")
     ap.add_argument("--autotune", action="store_true", help="print the shape sweep for the workload")

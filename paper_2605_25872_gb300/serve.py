@@ -55,6 +55,7 @@ class PoolSpec:
     res_sweeps_per_emcs: int = 240
     pretherm_sweeps: int = 960
     spin_layout: str = "bytes"      # "bits": 8x less spin memory per slot
+    tuning: dict | None = None      # kernel shape (Batch.set_tuning), e.g. the autotuner's
 
     def updates_per_emcs_per_sample(self):
         V = self.L ** 3
@@ -67,18 +68,26 @@ class GpuPool:
 
     def __init__(self, spec: PoolSpec, device="cuda", graph=True):
         import torch
-        from .batch import Batch, BatchConfig
+        from .batch import Batch
         self.spec = spec
         self.stream = torch.cuda.Stream(device)
-        self.cfg = BatchConfig(L=spec.L, n_samples=spec.slots, n_temps=spec.n_temps,
-                               t_min=spec.t_min, t_max=spec.t_max, n_replicas=spec.n_replicas,
-                               n_res=spec.n_res, sweeps_per_emcs=spec.sweeps_per_emcs,
-                               res_sweeps_per_emcs=spec.res_sweeps_per_emcs,
-                               er_on=spec.n_res > 0, cluster="acu", spin_layout=spec.spin_layout)
+        self.cfg = self.config_of(spec)
         self.batch = Batch(self.cfg, device=device, stream=self.stream)
+        if spec.tuning:
+            self.batch.set_tuning(**spec.tuning)
         self.batch.set_active(0, spec.slots, False)
         self.graph = graph
         self.event = torch.cuda.Event()
+
+    @staticmethod
+    def config_of(spec: PoolSpec):
+        """The batch configuration of a pool."""
+        from .batch import BatchConfig
+        return BatchConfig(L=spec.L, n_samples=spec.slots, n_temps=spec.n_temps,
+                           t_min=spec.t_min, t_max=spec.t_max, n_replicas=spec.n_replicas,
+                           n_res=spec.n_res, sweeps_per_emcs=spec.sweeps_per_emcs,
+                           res_sweeps_per_emcs=spec.res_sweeps_per_emcs,
+                           er_on=spec.n_res > 0, cluster="acu", spin_layout=spec.spin_layout)
 
     def reset(self, slot, req: Request):
         self.reset_many([slot], [req])
