@@ -625,14 +625,6 @@ def micsa_measure(dev, J, seeds, n_emcs=10):
     cfg = dataclasses.replace(batch_config(len(seeds)), rule="micsa")
     stream = torch.cuda.Stream(dev)
     b = Batch(cfg, couplings=J, seeds=seeds, device=dev, stream=stream)
-    tuned_shape = None
-    if args.tuned:
-        # the autotuner's shape for this configuration (measured on this GPU
-        # on a scratch batch; shapes never change results)
-        from paper_2605_25872_gb300.autotune import autotune
-        tuned_shape = autotune(cfg, device=dev)
-        if tuned_shape:
-            b.set_tuning(**tuned_shape)
     if WL.er_on and WL.res_pretherm_sweeps:
         b.prethermalize(WL.res_pretherm_sweeps)
     b.emcs(3, graph=True)
