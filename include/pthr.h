@@ -299,7 +299,10 @@ PTHR_API pthr_status pthr_set_active(pthr_batch *b, int first, int count, int ac
  * EMCS on its own stream, forked from and joined to `stream`.
  * pthr_group_emcs replays the graph n times on `stream`, after the work
  * already queued on every member's own stream and before the work queued on
- * them later (events), so per-batch calls and group EMCS may be mixed.  The
+ * them later (events), so per-batch calls and group EMCS may be mixed.
+ * Inside the caller's own capture of `stream` the four-launch form enqueues
+ * its kernels (captured in order, no events); the per-batch-graph form then
+ * returns PTHR_E_STATE without touching the capture.  The
  * batches must be at an EMCS boundary, must not be destroyed before the
  * group, and their idle slots cost no work.  Kernel shapes are fixed at
  * creation.  Results are those of stepping every batch alone. */

@@ -748,6 +748,7 @@ struct pthr_group {
     cudaGraphExec_t exec;
     int n;
     int launches;   // kernel launches per EMCS in the graph
+    int fused;      // 1: the four-launch form (group kernels), 0: per-batch graphs
     pthr_batch **batches;   // [n] members, for ordering against their own streams
     cudaEvent_t *ev_in;     // [n] work queued on each member's stream
     cudaEvent_t ev_out;     // the group's EMCS, for the members' later work
@@ -758,13 +759,14 @@ namespace {
 // A new group handle with its ordering events; nullptr if an event could not
 // be created (then nothing is left allocated).
 pthr_group *new_group(pthr_batch *const *batches, int n, cudaStream_t st, cudaGraph_t g, cudaGraphExec_t exec,
-                      int launches) {
+                      int launches, int fused) {
     pthr_group *grp = new pthr_group();
     grp->stream = st;
     grp->graph = g;
     grp->exec = exec;
     grp->n = n;
     grp->launches = launches;
+    grp->fused = fused;
     grp->batches = new pthr_batch *[n];
     grp->ev_in = new cudaEvent_t[n]();
     grp->ev_out = nullptr;
@@ -896,7 +898,7 @@ PTHR_API pthr_status pthr_group_create(pthr_batch *const *batches, int n, void *
             cudaGraphExec_t exec = nullptr;
             e = cudaGraphInstantiate(&exec, g, 0);
             if (e != cudaSuccess) { cudaGraphDestroy(g); return cuda_fail(nullptr, e, "group graph instantiate"); }
-            pthr_group *grp = new_group(batches, n, master, g, exec, launches);
+            pthr_group *grp = new_group(batches, n, master, g, exec, launches, 1);
             if (!grp) {
                 cudaGraphExecDestroy(exec);
                 cudaGraphDestroy(g);
@@ -944,7 +946,7 @@ PTHR_API pthr_status pthr_group_create(pthr_batch *const *batches, int n, void *
     int launches = 0;
     for (int i = 0; i < n; ++i)
         launches += 2 + (batches[i]->cfg.cluster_mode != PTHR_CLUSTER_OFF && batches[i]->dev.n_acu > 0) + 1;
-    pthr_group *grp = new_group(batches, n, master, g, exec, launches);
+    pthr_group *grp = new_group(batches, n, master, g, exec, launches, 0);
     if (!grp) {
         cudaGraphExecDestroy(exec);
         cudaGraphDestroy(g);
@@ -964,6 +966,19 @@ PTHR_API pthr_status pthr_group_emcs(pthr_group *g, int n) {
     PTHR_TRACE("pthr_group_emcs");
     if (!g || n < 0) return fail(nullptr, PTHR_E_INVAL, "bad group or count");
     if (n == 0) return PTHR_OK;
+    if (capturing(g->stream)) {
+        // inside the caller's capture a graph cannot be launched: the
+        // four-launch form enqueues its kernels instead (the capture orders
+        // them); the per-batch-graph form cannot be captured
+        if (!g->fused)
+            return fail(nullptr, PTHR_E_STATE, "this group runs per-batch graphs and cannot be captured");
+        for (int i = 0; i < n; ++i) {
+            int launches = 0;
+            const pthr_status st = group_fused_emcs(g->batches, g->n, g->stream, &launches);
+            if (st != PTHR_OK) return fail(nullptr, st, "group kernels could not be enqueued in the capture");
+        }
+        return PTHR_OK;
+    }
     // after the work already queued on every member's stream ...
     for (int i = 0; i < g->n; ++i) {
         cudaError_t e = cudaEventRecord(g->ev_in[i], g->batches[i]->stream);

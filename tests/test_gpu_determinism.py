@@ -135,3 +135,33 @@ def test_group_emcs_is_ordered_with_the_members_streams():
     torch.cuda.synchronize()
     for a, b in zip(free, synced):
         assert_same(state(a), state(b), f"L={a.cfg.L}")
+
+
+def test_group_emcs_inside_a_callers_graph_capture():
+    """pthr_group_emcs inside the caller's CUDA-graph capture: the four-launch
+    group enqueues its kernels into the capture (a graph cannot be launched
+    there), and replaying the caller's graph gives the state of direct calls."""
+    from paper_2605_25872_gb300.batch import Group
+
+    def members():
+        out = []
+        for i, L in enumerate((6, 10)):
+            cfg = BatchConfig(L=L, n_samples=16, n_temps=12, n_replicas=4, n_res=2, sweeps_per_emcs=2,
+                              res_sweeps_per_emcs=24)
+            out.append(Batch(cfg, couplings=W.gaussian_couplings(L, 16, 80 + i),
+                             seeds=W.sample_seeds(W.SEED_BASE + 80 + i, 16), stream=torch.cuda.Stream()))
+        torch.cuda.synchronize()
+        return out
+
+    direct, captured = members(), members()
+    gd, gc = Group(direct), Group(captured)
+    gd.emcs(3)
+    gd.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=gc.stream):
+        gc.emcs(1)
+    for _ in range(3):
+        graph.replay()
+    torch.cuda.synchronize()
+    for a, b in zip(direct, captured):
+        assert_same(state(a), state(b), f"L={a.cfg.L}")
