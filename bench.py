@@ -730,7 +730,8 @@ def main():
     ap.add_argument("--no-extras", action="store_true",
                     help="time the batched EMCS only (no plain form, e2e, CPU baseline)")
     ap.add_argument("--serve", action="store_true", help="serving mode (separate JSON line)")
-    ap.add_argument("--serve-budget", type=int, default=100, help="EMCS per request (serving)")
+    ap.add_argument("--serve-budget", type=int, default=10000,
+                    help="EMCS per request (serving; 10^4 EMCS = the 10^5-sweep budget of the serving workload)")
     ap.add_argument("--serve-requests", type=int, default=200)
     ap.add_argument("--serve-mem-gb", type=float, default=2.0)
     ap.add_argument("--serve-max-slots", type=int, default=128)

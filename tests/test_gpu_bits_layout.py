@@ -150,3 +150,33 @@ def test_spin_layout_autotuner_times_both_layouts():
     assert all(t["ms_per_emcs"] > 0 for t in table.values())
     # any slowdown is accepted once memory counts for more than it
     assert autotune_spin_layout(cfg, emcs=1, warm_emcs=1, memory_weight=1e9)[0] == "bits"
+
+
+def test_bits_reset_samples_and_checkpoint_equal_bytes():
+    """The serving admission path (a slot becomes a new sample, pre-thermalised)
+    and a checkpoint round trip in both layouts."""
+    cfg = BatchConfig(L=12, n_samples=4, n_temps=8, n_replicas=4, n_res=2, sweeps_per_emcs=2,
+                      res_sweeps_per_emcs=8)
+    a, b = pair(cfg, seed=33)
+    new_seeds = W.sample_seeds(W.SEED_BASE + 999, 2)
+    new_J = W.gaussian_couplings(cfg.L, 2, 999)
+    for x in (a, b):
+        x.emcs(2)
+        x.reset_samples(1, 2, seeds=new_seeds, couplings=new_J, pretherm_sweeps=16)
+        x.emcs(2)
+        x.synchronize()
+    assert_same_state(a, b)
+    blobs = [x.save() for x in (a, b)]
+    for x in (a, b):
+        x.emcs(3)
+        x.synchronize()
+    after = [x.export_spins().cpu().numpy() for x in (a, b)]
+    np.testing.assert_array_equal(after[0], after[1])
+    for x, blob in zip((a, b), blobs):
+        x.load(blob)
+        x.emcs(3)
+        x.synchronize()
+    # resume from the checkpoint repeats the same three EMCS exactly
+    np.testing.assert_array_equal(a.export_spins().cpu().numpy(), after[0])
+    np.testing.assert_array_equal(b.export_spins().cpu().numpy(), after[1])
+    assert_same_state(a, b)
