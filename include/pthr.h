@@ -26,6 +26,8 @@
  *    returned by the next pthr_poll().
  *  - Calls on one handle are not thread-safe; different handles are
  *    independent.  pthr_last_error() describes the last failure.
+ *  - Every call that enqueues GPU work opens an NVTX range named after
+ *    itself (no cost unless a profiler is attached).
  *
  * Geometry: site i = x + L*(y + L*z), 0 <= x,y,z < L, L even.  Couplings
  * J[s][mu][i] (mu = 0,1,2 for x,y,z) belong to the bond (i, i + e_mu) of
