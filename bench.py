@@ -313,6 +313,15 @@ def run_gpu(args):
 
     cfg = batch_config(args.samples)
     S = cfg.n_samples
+    schedule = None
+    if args.tuned_schedule:
+        # the schedule autotuner's cluster-move interval (the smallest whose
+        # cluster step is at most 10% of the EMCS on this GPU); it changes the
+        # Markov chain, so only this explicitly labelled line uses it
+        import dataclasses
+        from paper_2605_25872_gb300.autotune import autotune_schedule
+        k, schedule = autotune_schedule(cfg, device=dev)
+        cfg = dataclasses.replace(cfg, acu_interval=int(k))
     from paper_2605_25872_gb300.shard import shard_seeds
     seeds = shard_seeds(W.batch_seed(WL.index), rank, world, world * S)   # global sample ids
     J = W.gaussian_couplings(WL.L, S, W.batch_seed(WL.index) + rank)
@@ -390,7 +399,8 @@ def run_gpu(args):
         if rank == 0:
             print(json.dumps({"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                               "updates_per_ns_graph": world * upd / (ms_gr * 1e6),
-                              "shape": tuned_shape or "default",
+                              "shape": tuned_shape or "default", "acu_interval": cfg.acu_interval,
+                              **({"schedule": schedule} if schedule else {}),
                               "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
                               "samples": S, "phase_ms_sweep": ms_sweep,
                               "phase_ms": {n: float(phase[:, i].mean()) for i, n in
@@ -744,6 +754,9 @@ def main():
                     help="c4 (L=16 PTHR, the headline) or the batched L=8 / L=12 workloads")
     ap.add_argument("--spin-layout", default="bytes", choices=["bytes", "bits"],
                     help="spin storage in device memory (bits: 8x smaller; same results)")
+    ap.add_argument("--tuned-schedule", action="store_true",
+                    help="apply the schedule autotuner's cluster-move interval (a different Markov chain "
+                         "schedule; profiling lines only)")
     ap.add_argument("--tuned", action="store_true",
                     help="apply the autotuned kernel shape of the workload before timing")
     ap.add_argument("--rule", default="metropolis", choices=["metropolis", "heatbath", "micsa"],
@@ -755,6 +768,8 @@ def main():
     SPINS = args.spin_layout
     if RULE != "metropolis" and not args.no_extras:
         ap.error("--rule other than metropolis is for --no-extras profiling runs")
+    if args.tuned_schedule and not args.no_extras:
+        ap.error("--tuned-schedule is for --no-extras profiling runs")
     if args.workload != "c4":
         global METRIC
         METRIC = METRIC_OTHER.format(L=WL.L)
