@@ -165,3 +165,52 @@ def test_group_emcs_inside_a_callers_graph_capture():
     torch.cuda.synchronize()
     for a, b in zip(direct, captured):
         assert_same(state(a), state(b), f"L={a.cfg.L}")
+
+
+def test_batch_emcs_inside_a_callers_graph_capture():
+    """pthr_emcs(use_graph=1) while the caller captures the batch's stream
+    enqueues the EMCS kernels into that capture instead of its own graph."""
+    cfg = BatchConfig(L=8, n_samples=8, n_temps=8, n_replicas=4, n_res=2, sweeps_per_emcs=2,
+                      res_sweeps_per_emcs=16)
+    J, seeds = W.gaussian_couplings(8, 8, 90), W.sample_seeds(W.SEED_BASE + 90, 8)
+    direct = Batch(cfg, couplings=J, seeds=seeds, stream=torch.cuda.Stream())
+    captured = Batch(cfg, couplings=J, seeds=seeds, stream=torch.cuda.Stream())
+    torch.cuda.synchronize()
+    direct.emcs(4)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=captured.stream):
+        captured.emcs(2, graph=True)
+    for _ in range(2):
+        graph.replay()
+    torch.cuda.synchronize()
+    assert_same(state(direct), state(captured), "captured EMCS")
+
+
+def test_per_batch_graph_group_refuses_a_callers_capture():
+    """A group outside the four-launch form (an L=18 member) returns
+    PTHR_E_STATE inside a caller's capture, leaves the capture usable, and
+    still steps normally afterwards."""
+    from paper_2605_25872_gb300 import _lib
+    from paper_2605_25872_gb300.batch import Group
+    bs = []
+    for i, L in enumerate((18, 6)):
+        cfg = BatchConfig(L=L, n_samples=2, n_temps=6, n_replicas=4, n_res=2, sweeps_per_emcs=1,
+                          res_sweeps_per_emcs=4)
+        bs.append(Batch(cfg, couplings=W.gaussian_couplings(L, 2, 95 + i),
+                        seeds=W.sample_seeds(W.SEED_BASE + 95 + i, 2), stream=torch.cuda.Stream()))
+    torch.cuda.synchronize()
+    g = Group(bs)
+    assert g.launches_per_emcs > 4
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=g.stream):
+        with pytest.raises(_lib.PthrError) as err:
+            g.emcs(1)
+        x = torch.zeros(4, device="cuda")
+        x += 1                                  # the capture still records work
+    assert err.value.status == _lib.PTHR_E_STATE
+    graph.replay()
+    torch.cuda.synchronize()
+    assert float(x.sum()) == 4.0
+    g.emcs(1)
+    g.synchronize()
+    assert all(int(b.emcs_counter.cpu()[0]) == 1 for b in bs)
