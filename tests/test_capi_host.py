@@ -119,3 +119,53 @@ def test_measure_peak_rejects_bad_arguments_without_cuda(lib):
     # the L2 benchmark needs at least 1 MB past the 4 KB of sink words
     assert lib.pthr_measure_peak(_lib.PEAK_L2_READ, ctypes.c_void_p(256), 8192, None, ctypes.byref(r),
                                  ctypes.byref(t)) == _lib.PTHR_E_INVAL
+
+
+def test_random_configs_are_either_valid_with_a_consistent_layout_or_refused(lib):
+    """Random configurations (host-only, no CUDA): every one is either
+    accepted, with sub-buffers that are 256-byte aligned, in order, sized by
+    the configuration and inside the total, or refused with PTHR_E_INVAL and
+    a message, as the documented rules say."""
+    import numpy as np
+    rng = np.random.default_rng(7)
+    accepted = refused = 0
+    def pick(good, bad):
+        """a valid value mostly, an edge or invalid one 10% of the time"""
+        return int(rng.choice(bad)) if rng.random() < 0.1 else int(rng.choice(good))
+
+    for _ in range(600):
+        c = _lib.Config(pick([2, 4, 6, 8, 12, 16, 24], [0, 3, 13, 26, -2]), pick([1, 3, 64], [0, -1]),
+                        pick([2, 5, 32], [0, 1, 300]), pick([1, 2, 4, 32], [0, 3, 33]), pick([0, 1, 4], [-1, 255]),
+                        pick([0, 1, 10], [-1, 1 << 22]), pick([0, 240], [-1, 1 << 22]), pick([1, 8], [0, -3]),
+                        pick([0, 1, 2], [3, -1]), pick([0, 1, 2], [3, -1]), pick([0, 1], [0, 1]),
+                        pick([0, 1], [2, -1]), float(rng.choice([0.2, 0.5, -0.1, 0.0])),
+                        float(rng.choice([1.6, 2.0, 0.1])), 1.0, 5)
+        valid = (2 <= c.L <= 24 and c.L % 2 == 0 and c.n_samples >= 1 and c.n_temps >= 2
+                 and 1 <= c.n_replicas <= 32 and c.n_res >= 0 and c.n_temps + c.n_res <= 256
+                 and not (c.er_on and c.n_res < 1) and 0 <= c.sweeps_per_emcs < (1 << 22)
+                 and 0 <= c.res_sweeps_per_emcs < (1 << 22) and c.acu_interval >= 1
+                 and c.update_rule in (0, 1, 2)
+                 and c.cluster_mode in (0, 1, 2)
+                 and not (c.cluster_mode != 0 and (c.n_replicas < 2 or c.n_replicas % 2))
+                 and c.t_min > 0 and c.t_max > c.t_min and c.spin_layout in (0, 1))
+        n = ctypes.c_size_t()
+        st = lib.pthr_required_bytes(ctypes.byref(c), ctypes.byref(n))
+        if not valid:
+            assert st == _lib.PTHR_E_INVAL and len(lib.pthr_last_error(None)) > 0
+            refused += 1
+            continue
+        assert st == _lib.PTHR_OK
+        accepted += 1
+        end = 0
+        for buf in range(_lib.NBUF):
+            off, size = ctypes.c_size_t(), ctypes.c_size_t()
+            assert lib.pthr_buffer_info(ctypes.byref(c), buf, ctypes.byref(off), ctypes.byref(size)) == 0
+            assert off.value % 256 == 0 and off.value >= end
+            end = off.value + size.value
+        assert end <= n.value
+        off, size = ctypes.c_size_t(), ctypes.c_size_t()
+        lib.pthr_buffer_info(ctypes.byref(c), _lib.BUF_SPINS, ctypes.byref(off), ctypes.byref(size))
+        lb = ctypes.c_size_t()
+        assert lib.pthr_lattice_storage_bytes(c.L, c.spin_layout, ctypes.byref(lb)) == 0
+        assert size.value == c.n_samples * c.n_replicas * (c.n_temps + c.n_res) * lb.value
+    assert accepted > 20 and refused > 20
