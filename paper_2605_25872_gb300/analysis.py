@@ -95,6 +95,7 @@ def run_binned(batch, t_max: int, n_bins: int, chaos: bool = False):
         batch.swap(True, batch.cfg.er_on)
         batch.measure(chaos=chaos)
         if t in ends:
+            batch.synchronize()          # the batch may run on its own stream
             out[ends[t]] = (batch.obs.cpu().numpy().copy(), batch.chaos.cpu().numpy().copy())
     return out
 
