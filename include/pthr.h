@@ -207,6 +207,16 @@ PTHR_API pthr_status pthr_set_stream(pthr_batch *b, void *stream);
 PTHR_API pthr_status pthr_set_tuning(pthr_batch *b, const pthr_tuning *t);
 PTHR_API pthr_status pthr_get_tuning(const pthr_batch *b, pthr_tuning *t);
 
+/* Switch the local update rule (PTHR_METROPOLIS, PTHR_HEATBATH, PTHR_MICSA)
+ * from the next sweep on.  The paper's PTHR* runs Metropolis for the early
+ * bins and the MicSA walker (App. A.1) for the late ones.  Only at an EMCS
+ * boundary (else PTHR_E_STATE); PTHR_E_INVAL for an unknown rule.  The sweep
+ * draws of each rule follow their own counter streams from then on; the
+ * batch's captured EMCS graph is rebuilt on the next graph replay.  A group
+ * created earlier keeps the rule it was created with (create it again).
+ * Host-only; no CUDA call besides releasing the old graph. */
+PTHR_API pthr_status pthr_set_update_rule(pthr_batch *b, int rule);
+
 /* Step (i) of the EMCS (Sec. 3; App. A.1): n_pt_sweeps full-lattice
  * checkerboard sweeps of every PT clone at its temperature and, at the same
  * time, n_res_sweeps sweeps of every reservoir clone at T_max, with the

@@ -29,7 +29,7 @@ MAX_L = 24
 
 # every exported entry point of include/pthr.h
 EXPORTS = ("pthr_required_bytes", "pthr_buffer_info", "pthr_lattice_bytes", "pthr_lattice_storage_bytes",
-           "pthr_create_batch",
+           "pthr_create_batch", "pthr_set_update_rule",
            "pthr_destroy", "pthr_set_stream", "pthr_set_tuning", "pthr_get_tuning", "pthr_sweep",
            "pthr_houdayer", "pthr_cluster_labels", "pthr_swap", "pthr_observables", "pthr_emcs",
            "pthr_prethermalize_reservoir", "pthr_poll", "pthr_export_spins", "pthr_import_spins",
@@ -84,6 +84,7 @@ def load(path: str | None = None):
         "pthr_buffer_info": [P(Config), i, P(sz), P(sz)],
         "pthr_lattice_bytes": [i, P(sz)],
         "pthr_lattice_storage_bytes": [i, i, P(sz)],
+        "pthr_set_update_rule": [vp, i],
         "pthr_create_batch": [P(Config), vp, sz, vp, vp, vp, P(vp)],
         "pthr_set_stream": [vp, vp],
         "pthr_set_tuning": [vp, P(Tuning)],

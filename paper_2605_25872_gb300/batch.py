@@ -284,6 +284,13 @@ class Batch:
                         cluster_iter_cap)
         check(self.lib.pthr_set_tuning(self.h, ctypes.byref(t)), self.h)
 
+    def set_rule(self, rule: str):
+        """Switch the local update rule at an EMCS boundary (the paper's PTHR*:
+        Metropolis early, MicSA for the late bins)."""
+        import dataclasses
+        check(self.lib.pthr_set_update_rule(self.h, RULES[rule]), self.h)
+        self.cfg = dataclasses.replace(self.cfg, rule=rule)
+
     def get_tuning(self) -> dict:
         t = _lib.Tuning()
         check(self.lib.pthr_get_tuning(self.h, ctypes.byref(t)), self.h)

@@ -506,6 +506,21 @@ PTHR_API pthr_status pthr_set_tuning(pthr_batch *b, const pthr_tuning *t) {
     return PTHR_OK;
 }
 
+PTHR_API pthr_status pthr_set_update_rule(pthr_batch *b, int rule) {
+    if (!b) return fail(nullptr, PTHR_E_INVAL, "NULL handle");
+    if (rule != PTHR_METROPOLIS && rule != PTHR_HEATBATH && rule != PTHR_MICSA)
+        return fail(b, PTHR_E_INVAL, "unknown update_rule %d", rule);
+    if (b->pt_sweep_off || b->res_sweep_off)
+        return fail(b, PTHR_E_STATE, "the update rule changes only at an EMCS boundary (call pthr_swap first)");
+    b->cfg.update_rule = rule;
+    b->dev.rule = rule;
+    // the captured EMCS graph holds the old rule's kernels
+    if (b->graph_exec) { cudaGraphExecDestroy(b->graph_exec); b->graph_exec = nullptr; }
+    if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
+    b->graph_ok = 0;
+    return PTHR_OK;
+}
+
 PTHR_API pthr_status pthr_get_tuning(const pthr_batch *b, pthr_tuning *t) {
     if (!b || !t) return fail(nullptr, PTHR_E_INVAL, "NULL argument");
     SweepShape sh = sweep_shape(b);

@@ -47,6 +47,8 @@ def parse_args(argv=None):
     ap.add_argument("--emcs", type=int, required=True, help="EMCS of the run (t_max)")
     ap.add_argument("--bins", type=int, default=4)
     ap.add_argument("--chaos", action="store_true", help="also accumulate the chaos overlaps (Sec. 5)")
+    ap.add_argument("--micsa-bins", type=int, default=0,
+                    help="PTHR*: the last N bins run with the MicSA walker (App. A.1)")
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--couplings", default=None, help=".npy file of FP32 couplings [S, 3, L^3]")
     ap.add_argument("--out", required=True, help="JSON-lines output file (appended)")
@@ -93,6 +95,8 @@ def run(args) -> dict:
     for i in order:
         lo, hi = bins[i]
         advance(lo - 1 - done)
+        if i < args.micsa_bins and b.cfg.rule != "micsa":
+            b.set_rule("micsa")           # PTHR*: the late bins with the walker
         b.synchronize()
         pt_prev = b.pt_accepted.cpu().numpy().copy()
         b.reset_observables()
@@ -106,6 +110,7 @@ def run(args) -> dict:
         X = chaos_from_accumulators(b.chaos.cpu().numpy(), obs, cfg.n_replicas) if args.chaos else None
         for r in recs:
             r["bin"] = i
+            r["rule"] = b.cfg.rule
             if X is not None:
                 v = X[r["sample"], r["k"]]
                 r["chaos_X"] = float(v) if np.isfinite(v) else None

@@ -107,6 +107,7 @@ def test_null_handle_calls_fail_cleanly(lib):
     assert lib.pthr_houdayer(None) == _lib.PTHR_E_INVAL
     assert lib.pthr_emcs(None, 1, 0) == _lib.PTHR_E_INVAL
     assert lib.pthr_poll(None, 0) == _lib.PTHR_E_INVAL
+    assert lib.pthr_set_update_rule(None, 0) == _lib.PTHR_E_INVAL
     lib.pthr_destroy(None)
 
 

@@ -320,10 +320,16 @@ def diverged_samples(gpu, mir):
     return bad
 
 
-def run_emcs_parity(cfg, n_emcs, seed):
+def run_emcs_parity(cfg, n_emcs, seed, switch=None):
+    """switch = (EMCS index, rule): both sides change the local update rule
+    there (the paper's PTHR*: Metropolis early, MicSA late)."""
     gpu, mir = make(cfg, seed=seed)
     resyncs = 0
     for e in range(n_emcs):
+        if switch is not None and e == switch[0]:
+            gpu.set_rule(switch[1])
+            mir.rule = {"metropolis": O.RULE_METROPOLIS, "heatbath": O.RULE_HEATBATH,
+                        "micsa": O.RULE_MICSA}[switch[1]]
         gpu.sweep(cfg.sweeps_per_emcs, cfg.res_sweeps_per_emcs if cfg.er_on else 0)
         if cfg.cluster != "off":
             gpu.houdayer()
@@ -373,6 +379,20 @@ def test_full_emcs_parity_batched(cluster, rule, er):
                       sweeps_per_emcs=2, res_sweeps_per_emcs=6, er_on=er, cluster=cluster, rule=rule)
     gpu, mir, resyncs = run_emcs_parity(cfg, 40, seed=11)
     assert resyncs <= 2
+
+
+def test_update_rule_switch_at_an_emcs_boundary():
+    """PTHR*: Metropolis for 12 EMCS, then MicSA, against the oracle doing the
+    same; the switch is refused inside an EMCS."""
+    from paper_2605_25872_gb300 import _lib
+    cfg = BatchConfig(L=8, n_samples=3, n_temps=8, n_replicas=4, n_res=2, sweeps_per_emcs=2,
+                      res_sweeps_per_emcs=6)
+    gpu, mir, resyncs = run_emcs_parity(cfg, 24, seed=77, switch=(12, "micsa"))
+    assert resyncs <= 2 and gpu.cfg.rule == "micsa"
+    gpu.sweep(1, 0)
+    with pytest.raises(_lib.PthrError) as err:
+        gpu.set_rule("metropolis")
+    assert err.value.status == _lib.PTHR_E_STATE
 
 
 def test_acu_interval_and_threshold():
