@@ -7,6 +7,8 @@ then one summary record (tau_TRW of Sec. 5 over the run, throughput).
 
     python -m paper_2605_25872_gb300.run --L 12 --samples 64 --temps 24 \\
         --emcs 4096 --bins 6 --out run.jsonl
+    python -m paper_2605_25872_gb300.run --preset paper-L16 --samples 64 \\
+        --emcs 65536 --out l16.jsonl       # Table A1's L = 16 run, shortened
 
 Couplings are drawn on the device from each sample's seed (seed + s) unless
 --couplings names a .npy file of FP32 [S, 3, L^3] bonds.  Every step runs in
@@ -28,31 +30,60 @@ def temperatures(t_min: float, t_max: float, n: int) -> np.ndarray:
     return t_min + (k * (t_max - t_min)) / (n - 1)
 
 
+# The paper's production runs (App. A.2, Table A1): N_T temperatures uniform in
+# [T_min, T_max], 4 replica groups, the EMCS of Sec. 3 (10 sweeps, ACU below
+# T = 1, PT, ER with 4 reservoir clones at 240 sweeps).  L = 12 and 14 used
+# Metropolis (PTHR); L = 16 switched to MicSA (PTHR*) for bins 0 and 1; L = 18
+# used MicSA throughout.
+PRESETS = {
+    "paper-L12": dict(L=12, t_min=0.42, t_max=1.8, temps=24, samples=2048, emcs=2 ** 17, rule="metropolis",
+                      micsa_bins=0),
+    "paper-L14": dict(L=14, t_min=0.2, t_max=2.0, temps=48, samples=2000, emcs=6_400_000, rule="metropolis",
+                      micsa_bins=0),
+    "paper-L16": dict(L=16, t_min=0.2, t_max=2.0, temps=60, samples=2081, emcs=38_400_000, rule="metropolis",
+                      micsa_bins=2),
+    "paper-L18": dict(L=18, t_min=0.2, t_max=2.0, temps=72, samples=2028, emcs=34_800_000, rule="micsa",
+                      micsa_bins=0),
+}
+DEFAULTS = dict(samples=16, temps=24, t_min=0.2, t_max=1.6, rule="metropolis", micsa_bins=0)
+
+
 def parse_args(argv=None):
+    """Arguments given explicitly override the preset's, which override the
+    defaults."""
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
-    ap.add_argument("--L", type=int, required=True)
-    ap.add_argument("--samples", type=int, default=16)
-    ap.add_argument("--temps", type=int, default=24)
-    ap.add_argument("--t-min", type=float, default=0.2)
-    ap.add_argument("--t-max", type=float, default=1.6)
+    ap.add_argument("--preset", choices=sorted(PRESETS), default=None,
+                    help="a run of the paper's Table A1 (explicit arguments override it)")
+    ap.add_argument("--L", type=int, default=None)
+    ap.add_argument("--samples", type=int, default=None)
+    ap.add_argument("--temps", type=int, default=None)
+    ap.add_argument("--t-min", type=float, default=None)
+    ap.add_argument("--t-max", type=float, default=None)
     ap.add_argument("--replicas", type=int, default=4)
     ap.add_argument("--res", type=int, default=4, help="reservoir clones per replica group (0: no ER)")
     ap.add_argument("--sweeps", type=int, default=10, help="local sweeps per EMCS")
     ap.add_argument("--res-sweeps", type=int, default=240, help="reservoir sweeps per EMCS")
     ap.add_argument("--pretherm", type=int, default=960, help="reservoir pre-thermalisation sweeps")
-    ap.add_argument("--rule", default="metropolis", choices=["metropolis", "heatbath", "micsa"])
+    ap.add_argument("--rule", default=None, choices=["metropolis", "heatbath", "micsa"])
     ap.add_argument("--cluster", default="acu", choices=["acu", "single", "off"])
     ap.add_argument("--acu-interval", type=int, default=1)
     ap.add_argument("--spin-layout", default="bytes", choices=["bytes", "bits"])
-    ap.add_argument("--emcs", type=int, required=True, help="EMCS of the run (t_max)")
+    ap.add_argument("--emcs", type=int, default=None, help="EMCS of the run (t_max)")
     ap.add_argument("--bins", type=int, default=4)
     ap.add_argument("--chaos", action="store_true", help="also accumulate the chaos overlaps (Sec. 5)")
-    ap.add_argument("--micsa-bins", type=int, default=0,
+    ap.add_argument("--micsa-bins", type=int, default=None,
                     help="PTHR*: the last N bins run with the MicSA walker (App. A.1)")
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--couplings", default=None, help=".npy file of FP32 couplings [S, 3, L^3]")
     ap.add_argument("--out", required=True, help="JSON-lines output file (appended)")
-    return ap.parse_args(argv)
+    args = ap.parse_args(argv)
+    preset = PRESETS.get(args.preset, {})
+    for key in ("L", "samples", "temps", "t_min", "t_max", "emcs", "rule", "micsa_bins"):
+        if getattr(args, key) is None:
+            setattr(args, key, preset.get(key, DEFAULTS.get(key)))
+    if args.L is None or args.emcs is None:
+        ap.error("--L and --emcs are required without a preset")
+    return args
 
 
 def run(args) -> dict:
