@@ -1,6 +1,7 @@
 """Host logic of the serving loop (no GPU): admission by free slots,
 continuous batching, completion accounting, FIFO order per lattice size."""
 import numpy as np
+import pytest
 
 from paper_2605_25872_gb300.serve import PoolSpec, Request, Server
 
@@ -37,6 +38,7 @@ class FakePool:
 
     def free(self, slot):
         self.active[slot] = False
+        self.log.append(("free", slot))
 
 
 def test_requests_finish_with_their_budget_and_slots_are_reused():
@@ -129,3 +131,39 @@ def test_cancel_requested_from_outside_the_loop():
     done = srv.run(reqs, realtime=False)
     assert sorted(r.rid for r in done) == [0, 2]
     assert [r.rid for r in srv.cancelled] == [1]
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_random_streams_keep_the_serving_invariants(seed):
+    """Random arrivals, budgets, queue bounds and cancellations against the fake
+    pool: a finished request ran exactly its budget on its own slot state, no
+    slot ever holds two requests, cancelled and refused requests never finish,
+    and every request ends in exactly one of done / cancelled / refused."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    specs = [PoolSpec(L=6, slots=int(rng.integers(1, 4))), PoolSpec(L=8, slots=int(rng.integers(1, 3)))]
+    srv = Server(specs, pool_factory=FakePool, max_chunk=int(rng.integers(1, 9)),
+                 max_queue=int(rng.integers(2, 8)))
+    reqs = [Request(rid=i, L=int(rng.choice([6, 8])), seed=1000 + i, budget_emcs=int(rng.integers(1, 20)))
+            for i in range(40)]
+    for rid in rng.choice(40, size=8, replace=False):
+        srv.request_cancel(int(rid))
+    done = srv.run(reqs, realtime=False)
+    ids_done = {r.rid for r in done}
+    ids_cancel = {r.rid for r in srv.cancelled}
+    ids_refused = {r.rid for r in srv.refused}
+    assert ids_done | ids_cancel | ids_refused == set(range(40))
+    assert not (ids_done & ids_cancel) and not (ids_done & ids_refused) and not (ids_cancel & ids_refused)
+    for r in done:
+        seed_v, emcs = r.obs[0]
+        assert seed_v == r.seed and emcs == r.budget_emcs and not r.cancelled
+    for L, pool in srv.pools.items():
+        live = set()
+        for ev in pool.log:
+            if ev[0] == "reset":
+                assert ev[1] not in live
+                live.add(ev[1])
+            elif ev[0] == "free":
+                live.discard(ev[1])
+    st = srv.stats()
+    assert st["requests"] == len(done) and st["cancelled"] == len(ids_cancel) and st["refused"] == len(ids_refused)
